@@ -1,0 +1,39 @@
+"""Ogita-Aishima eigenpair refinement, one step, plain FP64 (test infrastructure).
+
+Ogita & Aishima, "Iterative refinement for symmetric eigenvalue decomposition",
+Japan J. Indust. Appl. Math. 35 (2018).  Given symmetric A and an approximate
+eigenvector matrix X:
+
+    R  = I - X^T X
+    S  = X^T A X
+    lam_i = s_ii / (1 - r_ii)
+    delta = 2 (||S - diag(lam)||_2 + ||A||_2 ||R||_2)
+    E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i)   if |lam_i - lam_j| > delta
+         = r_ij / 2                                 otherwise (including i == j)
+    X'  = X + X E
+
+The 2-norms in delta are replaced by Frobenius norms, which bound them from above
+(so the threshold can only grow; clustered pairs then fall into the r_ij/2 branch,
+which is the safe one).  Matrix products are numpy's FP64 matmul.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def refine(A, X):
+    """One refinement step.  Returns (lam, X_new, info) with info holding delta."""
+    A = np.asarray(A, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    n = A.shape[0]
+    R = np.eye(n) - X.T @ X
+    S = X.T @ (A @ X)
+    r = np.diag(R)
+    lam = np.diag(S) / (1.0 - r)
+    D = S - np.diag(lam)
+    delta = 2.0 * (np.linalg.norm(D) + np.linalg.norm(A) * np.linalg.norm(R))
+    diff = lam[None, :] - lam[:, None]          # diff[i, j] = lam_j - lam_i
+    far = np.abs(diff) > delta
+    E = np.where(far, (S + lam[None, :] * R) / np.where(far, diff, 1.0), 0.5 * R)
+    Xn = X + X @ E
+    return lam, Xn, {"delta": float(delta)}

@@ -1,0 +1,164 @@
+/*
+ * evd.h -- C ABI of libevd, a GB300 (sm_103a) two-stage symmetric eigensolver.
+ *
+ * Problem (Sec. 1): for a dense symmetric A (n x n), compute A = Q Lambda Q^T with
+ * Lambda = diag(w) ascending and Q orthogonal.  The method is the two-stage EVD of
+ * Sec. 2.1: successive band reduction (SBR, Sec. 2.1.1 and Eq. 1) to a band of
+ * half-width b, bulge chasing (BC, Sec. 2.1.1 and Sec. 4.2) to a tridiagonal T, a
+ * divide-and-conquer tridiagonal solve (Sec. 1, Sec. 3.3), and the back
+ * transformation (Sec. 2.1.2: BC-Back then SBR-Back, conventional order).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are FP64, column-major: element (i, j) at ptr[i + j*ld], ld >= n.
+ *   - Only the LOWER triangle of A is read (Sec. 4.1 keeps the lower triangle).
+ *   - All matrix and vector pointers are DEVICE pointers unless the argument
+ *     name ends in _host.  The caller owns every buffer (A, w, d, e, Q and the
+ *     workspace); the library never frees them.  A plan owns only small internal
+ *     state (status word, progress counters, tuning choices).
+ *   - Calls are asynchronous on the plan's stream.  Errors that the host can see
+ *     (bad sizes, null pointers, too small a workspace) return at once.  Errors
+ *     found on the device (non-finite input, a wait that timed out,
+ *     non-convergence) are latched in the plan's status word and returned by
+ *     evd_plan_status().  No call ever falls back to the CPU.
+ *   - No C++ exception crosses this ABI.
+ */
+#ifndef EVD_H_
+#define EVD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct evd_plan_s* evd_plan_t;
+
+typedef enum {
+  EVD_OK = 0,
+  EVD_ERR_INVALID_ARG = 1,     /* a size, leading dimension or pointer is invalid        */
+  EVD_ERR_WORKSPACE = 2,       /* workspace pointer null or smaller than required        */
+  EVD_ERR_OOM = 3,             /* the plan's small internal allocation failed            */
+  EVD_ERR_CUDA = 4,            /* a CUDA runtime call failed                             */
+  EVD_ERR_NONFINITE = 5,       /* the input held NaN or Inf (device check)               */
+  EVD_ERR_NO_CONVERGENCE = 6,  /* a tridiagonal leaf or secular root did not converge    */
+  EVD_ERR_TIMEOUT = 7,         /* a bounded device-side wait gave up                     */
+  EVD_ERR_NOT_SUPPORTED = 8    /* option not built for this GPU                          */
+} evd_status_t;
+
+typedef enum { EVD_VALUES = 0, EVD_VECTORS = 1 } evd_job_t;
+
+/* Arithmetic of the dense contractions (the SBR trailing update and Z formation
+ * of Eq. 1, the back-transformation GEMMs and the divide-and-conquer merges).
+ *   EVD_FP64        FP64-accurate products: FP64 operands split into 8 bfloat16
+ *                   slices of 7 bits, slice pairs multiplied on tensor cores with
+ *                   exact FP32 partial sums, recombined in 64-bit integers.
+ *   EVD_SPLIT_BF16  Split precision: 4 slices for those products, then
+ *                   Ogita-Aishima refinement with FP64-accurate residual products.
+ *   EVD_SPLIT_INT8  Accepted for interface completeness; GB300's INT8 tensor rate
+ *                   is far below its BF16 rate, so this returns EVD_ERR_NOT_SUPPORTED.
+ * Householder vectors and tau (panel QR, BC), the secular equation and the
+ * refinement residual products are FP64-accurate in every mode. */
+typedef enum { EVD_FP64 = 0, EVD_SPLIT_INT8 = 1, EVD_SPLIT_BF16 = 2 } evd_prec_t;
+
+/* Create a plan for n x n problems with leading dimension lda.
+ *   b   band half-width of SBR (Sec. 2.1.1; typical 32, Sec. 4.1).  0 = autotuned.
+ *   nb  outer (double-blocking) width of SBR, a multiple of b.       0 = autotuned.
+ *   stream  a cudaStream_t (passed as void*), NULL for the legacy default stream.
+ * Must be called with the target device current.  Returns EVD_ERR_INVALID_ARG for
+ * n < 0, lda < max(1, n), b < 0, nb < 0, b > 0 && nb % b != 0, or b > 128. */
+evd_status_t evd_plan_create(evd_plan_t* plan, int64_t n, int64_t lda, evd_job_t job,
+                             evd_prec_t prec, int b, int nb, void* stream);
+
+/* Bytes of device workspace every call on this plan needs (caller allocates,
+ * 256-byte aligned).  The same workspace must be passed to the stage calls of one
+ * solve, since later stages read what earlier stages left there. */
+evd_status_t evd_plan_workspace_size(evd_plan_t plan, size_t* bytes);
+
+/* The plan's chosen band width and double-blocking width. */
+evd_status_t evd_plan_get_blocking(evd_plan_t plan, int* b, int* nb);
+
+/* Stage 1 -- SBR (Sec. 2.1.1, Eq. 1): reduce the lower triangle of A to a band of
+ * half-width b.  A is overwritten: its band holds B, below the band it holds the
+ * panel Householder vectors (unit diagonal implied); their tau and T factors go to
+ * ws.  The band is also packed into ws for the next stage. */
+evd_status_t evd_sbr(evd_plan_t plan, double* A, void* ws);
+
+/* Stage 2 -- BC (Sec. 2.1.1, Sec. 4.2): reduce the band in ws to tridiagonal T.
+ * d (n) receives the diagonal, e (n-1) the sub-diagonal.  With EVD_VECTORS the BC
+ * Householder vectors and tau stay in ws for the back transformation. */
+evd_status_t evd_bulge_chase(evd_plan_t plan, void* ws, double* d, double* e);
+
+/* Stage 3 -- divide and conquer (Sec. 1, Sec. 3.3): on entry d (n), e (n-1) hold T;
+ * on exit d holds the eigenvalues ascending.  e is destroyed.  If Qd != NULL it
+ * receives the n x n eigenvector matrix of T (ldq >= n). */
+evd_status_t evd_tridiag_solve(evd_plan_t plan, double* d, double* e, double* Qd, int64_t ldq,
+                               void* ws);
+
+/* Stage 4 -- back transformation (Sec. 2.1.2, conventional order): on entry Q holds
+ * Q_d; on exit Q = Q_s Q_b Q_d, the eigenvectors of the A given to evd_sbr.  Reads
+ * the SBR vectors from the A passed to evd_sbr (still needed: pass it again) and
+ * the BC vectors from ws. */
+evd_status_t evd_back_transform(evd_plan_t plan, const double* A_reduced, void* ws, double* Q,
+                                int64_t ldq);
+
+/* The whole path: stages 1-4 (stage 4 only with EVD_VECTORS), plus refinement for
+ * EVD_SPLIT_BF16.  A is overwritten (as in LAPACK syevd) -- except for the split
+ * mode, which first copies A into ws for the refinement residuals.  w (n) receives
+ * the eigenvalues ascending; Q (n x n, ldq) the eigenvectors (may be NULL for
+ * EVD_VALUES). */
+evd_status_t evd_syevd(evd_plan_t plan, double* A, double* w, double* Q, int64_t ldq, void* ws);
+
+/* Ogita-Aishima refinement (one or more steps) of an approximate eigendecomposition
+ * of the symmetric A0 (lower triangle read, lda = the plan's): Q (in/out, ldq) and
+ * w (out).  Residual products are FP64-accurate.  Uses ws. */
+evd_status_t evd_refine(evd_plan_t plan, const double* A0, double* w, double* Q, int64_t ldq,
+                        int iterations, void* ws);
+
+/* Sync the plan's stream and read its device status word.  *info receives a
+ * stage-specific index (e.g. the leaf or root that failed), 0 if none.  Clears the
+ * status word. */
+evd_status_t evd_plan_status(evd_plan_t plan, int* info);
+
+/* Destroy a plan (syncs its stream first).  NULL is a no-op. */
+void evd_plan_destroy(evd_plan_t plan);
+
+/* Static text for a status code. */
+const char* evd_status_string(evd_status_t status);
+
+/* ---------------------------------------------------------------------------
+ * Batched solve: count independent symmetric problems of uneven size, each with
+ * its own A (lower read, overwritten), lda, w, Q, ldq, in one captured CUDA graph
+ * whose kernels are persistent and walk a longest-first work queue.  Arrays n, lda,
+ * ldq are HOST arrays of length count; A, w, Q are HOST arrays of DEVICE pointers.
+ * ws/ws_bytes: device workspace of at least evd_batched_workspace_size().
+ * ------------------------------------------------------------------------- */
+evd_status_t evd_batched_workspace_size(int count, const int64_t* n_host, evd_job_t job,
+                                        size_t* bytes);
+evd_status_t evd_syevd_batched(int count, const int64_t* n_host, double* const* A_host,
+                               const int64_t* lda_host, double* const* w_host,
+                               double* const* Q_host, const int64_t* ldq_host, evd_job_t job,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * The dense product engine on its own (for tests and benchmarks):
+ *   C = alpha * op(A) * op(B) + beta * C, FP64 column-major, op = N or T.
+ * slices: 0 = plain FP64 CUDA-core kernel; 1..8 = tensor-core product with that many
+ * 7-bit bfloat16 slices per operand (8 = FP64-accurate).  ws must hold
+ * evd_gemm_workspace_size() bytes.  Runs on `stream`. */
+evd_status_t evd_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int slices, size_t* bytes);
+evd_status_t evd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                       const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                       double* C, int64_t ldc, int slices, void* ws, size_t ws_bytes,
+                       void* stream);
+
+/* Autotuner: time candidate (b, nb) in {32, 64, 128}^2, nb >= b, for an n x n
+ * problem and cache the winner in the JSON file at cache_path (NULL = no cache).
+ * Allocates its own scratch with cudaMalloc.  Returns the choice in *b, *nb. */
+evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char* cache_path,
+                          int* b, int* nb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVD_H_ */

@@ -1,0 +1,418 @@
+// C ABI of libevd: plans, workspace layout, the stage calls and the whole path.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "evd_internal.h"
+
+using namespace evd;
+
+namespace evd {
+int64_t bc_num_reflectors(int64_t n, int b);
+}
+
+struct WsLayout {
+  // persistent across the stages of one solve
+  double* sbr_tau = nullptr;
+  double* sbr_T = nullptr;
+  double* band = nullptr;
+  double* U = nullptr;
+  double* Utau = nullptr;
+  double* A0 = nullptr;     // split mode: copy of A for the refinement residuals
+  double* Qd_int = nullptr; // values-only: D&C still forms Q_d here
+  double* e = nullptr;      // sub-diagonal of T between BC and D&C
+  // union region
+  char* uni = nullptr;
+  size_t uni_bytes = 0;
+  void* gemm_ws = nullptr;
+  size_t gemm_bytes = 0;
+  size_t total = 0;
+};
+
+struct evd_plan_s {
+  PlanCore core;
+  int* d_status = nullptr;   // kStatusWords ints
+  unsigned* d_bar = nullptr; // 2 words
+  int* d_prog = nullptr;     // n ints
+  bool own_stream = false;
+};
+
+namespace {
+
+int64_t n_panels(int64_t n, int b) {
+  int64_t np = 0;
+  while (n - (np * b + b) >= 2) ++np;
+  return np;
+}
+
+constexpr int kMaxPanelCtas = 2048;
+
+size_t sbr_union_bytes(int64_t n, int b) {
+  Carver c(nullptr);
+  c.take<double>((size_t)n * b);  // V
+  c.take<double>((size_t)n * b);  // W
+  c.take<double>((size_t)n * b);  // Z
+  c.take<double>((size_t)n * b);  // Y
+  c.take<double>((size_t)b * b * 4);
+  c.take<double>((size_t)2 * kMaxPanelCtas * (1 + b) + (size_t)b * b);
+  return c.off;
+}
+size_t dc_union_bytes(int64_t n) {
+  Carver c(nullptr);
+  c.take<double>((size_t)n * n);
+  c.take<double>((size_t)n * n);
+  c.take<double>((size_t)n * n);
+  c.take<double>((size_t)10 * n + 8);
+  c.take<int>((size_t)32 * n + 1024);
+  return c.off;
+}
+size_t back_union_bytes(int64_t n, int b) {
+  Carver c(nullptr);
+  c.take<double>((size_t)n * b);
+  c.take<double>((size_t)n * b);
+  c.take<double>((size_t)n * b);
+  return c.off;
+}
+size_t refine_union_bytes(int64_t n) {
+  Carver c(nullptr);
+  c.take<double>((size_t)n * n);
+  c.take<double>((size_t)n * n);
+  c.take<double>((size_t)n * n);
+  c.take<double>((size_t)4 * n + 8);
+  return c.off;
+}
+
+WsLayout make_layout(const PlanCore& pc, void* ws) {
+  WsLayout L;
+  const int64_t n = pc.n;
+  const int b = pc.b;
+  Carver c(ws);
+  L.sbr_tau = c.take<double>((size_t)std::max<int64_t>(n, 1));
+  L.sbr_T = c.take<double>((size_t)std::max<int64_t>(n_panels(n, b), 1) * b * b);
+  L.band = c.take<double>((size_t)(2 * b + 1) * std::max<int64_t>(n, 1));
+  L.e = c.take<double>((size_t)std::max<int64_t>(n, 1));
+  if (pc.job == EVD_VECTORS) {
+    int64_t nref = bc_num_reflectors(n, b);
+    L.U = c.take<double>((size_t)std::max<int64_t>(nref, 1) * b);
+    L.Utau = c.take<double>((size_t)std::max<int64_t>(nref, 1));
+  } else {
+    L.Qd_int = c.take<double>((size_t)n * n);
+  }
+  if (pc.prec == EVD_SPLIT_BF16) L.A0 = c.take<double>((size_t)n * n);
+  size_t ub = std::max({sbr_union_bytes(n, b), dc_union_bytes(n), back_union_bytes(n, b),
+                        pc.prec == EVD_SPLIT_BF16 ? refine_union_bytes(n) : (size_t)0});
+  L.uni = c.take<char>(ub);
+  L.uni_bytes = ub;
+  size_t gb = std::max(gemm_scratch_bytes(n, n, n, pc.slices),
+                       pc.prec == EVD_SPLIT_BF16 ? gemm_scratch_bytes(n, n, n, pc.ref_slices) : (size_t)0);
+  L.gemm_ws = c.take<char>(gb);
+  L.gemm_bytes = gb;
+  L.total = align_up(c.off, 256);
+  return L;
+}
+
+SbrWork sbr_work(const evd_plan_s* p, const WsLayout& L) {
+  const int64_t n = p->core.n;
+  const int b = p->core.b;
+  Carver c(L.uni);
+  SbrWork w;
+  w.tau = L.sbr_tau;
+  w.T = L.sbr_T;
+  w.V = c.take<double>((size_t)n * b);
+  w.W = c.take<double>((size_t)n * b);
+  w.Z = c.take<double>((size_t)n * b);
+  w.Y = c.take<double>((size_t)n * b);
+  w.M = c.take<double>((size_t)b * b * 4);
+  w.partial = c.take<double>((size_t)2 * kMaxPanelCtas * (1 + b) + (size_t)b * b);
+  w.bar = p->d_bar;
+  w.band = L.band;
+  w.gemm_ws = L.gemm_ws;
+  w.gemm_ws_bytes = L.gemm_bytes;
+  return w;
+}
+
+BcWork bc_work(const evd_plan_s* p, const WsLayout& L) {
+  BcWork w;
+  w.band = L.band;
+  w.U = L.U;
+  w.Utau = L.Utau;
+  w.off = nullptr;
+  w.prog = p->d_prog;
+  w.bar = p->d_bar;
+  return w;
+}
+
+DcWork dc_work(const evd_plan_s* p, const WsLayout& L) {
+  const int64_t n = p->core.n;
+  Carver c(L.uni);
+  DcWork w;
+  w.Qtmp = c.take<double>((size_t)n * n);
+  w.Qn = c.take<double>((size_t)n * n);
+  w.Umat = c.take<double>((size_t)n * n);
+  w.vec = c.take<double>((size_t)10 * n + 8);
+  w.ivec = c.take<int>((size_t)32 * n + 1024);
+  w.gemm_ws = L.gemm_ws;
+  w.gemm_ws_bytes = L.gemm_bytes;
+  return w;
+}
+
+BackWork back_work(const evd_plan_s* p, const WsLayout& L) {
+  const int64_t n = p->core.n;
+  const int b = p->core.b;
+  Carver c(L.uni);
+  BackWork w;
+  w.Tg = nullptr;
+  w.Vp = c.take<double>((size_t)n * b);
+  w.Wp = c.take<double>((size_t)n * b);
+  w.Tp = c.take<double>((size_t)n * b);
+  w.gemm_ws = L.gemm_ws;
+  w.gemm_ws_bytes = L.gemm_bytes;
+  return w;
+}
+
+RefineWork refine_work(const evd_plan_s* p, const WsLayout& L) {
+  const int64_t n = p->core.n;
+  Carver c(L.uni);
+  RefineWork w;
+  w.R = c.take<double>((size_t)n * n);
+  w.S = c.take<double>((size_t)n * n);
+  w.AX = c.take<double>((size_t)n * n);
+  w.E = nullptr;
+  w.vec = c.take<double>((size_t)4 * n + 8);
+  w.gemm_ws = L.gemm_ws;
+  w.gemm_ws_bytes = L.gemm_bytes;
+  return w;
+}
+
+evd_status_t check_ws(const evd_plan_s* p, void* ws) {
+  if (!ws && p->core.n > 0) return EVD_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return EVD_ERR_WORKSPACE;
+  return EVD_OK;
+}
+
+int default_b(int64_t n) { return n >= 4096 ? 64 : 32; }
+
+}  // namespace
+
+extern "C" {
+
+const char* evd_status_string(evd_status_t s) {
+  switch (s) {
+    case EVD_OK: return "EVD_OK";
+    case EVD_ERR_INVALID_ARG: return "EVD_ERR_INVALID_ARG";
+    case EVD_ERR_WORKSPACE: return "EVD_ERR_WORKSPACE";
+    case EVD_ERR_OOM: return "EVD_ERR_OOM";
+    case EVD_ERR_CUDA: return "EVD_ERR_CUDA";
+    case EVD_ERR_NONFINITE: return "EVD_ERR_NONFINITE";
+    case EVD_ERR_NO_CONVERGENCE: return "EVD_ERR_NO_CONVERGENCE";
+    case EVD_ERR_TIMEOUT: return "EVD_ERR_TIMEOUT";
+    case EVD_ERR_NOT_SUPPORTED: return "EVD_ERR_NOT_SUPPORTED";
+  }
+  return "EVD_ERR_UNKNOWN";
+}
+
+evd_status_t evd_plan_create(evd_plan_t* plan, int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb,
+                             void* stream) {
+  if (!plan) return EVD_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (n < 0 || lda < std::max<int64_t>(1, n) || b < 0 || nb < 0 || b > 128) return EVD_ERR_INVALID_ARG;
+  if (b > 0 && nb > 0 && nb % b != 0) return EVD_ERR_INVALID_ARG;
+  if (job != EVD_VALUES && job != EVD_VECTORS) return EVD_ERR_INVALID_ARG;
+  if (prec == EVD_SPLIT_INT8) return EVD_ERR_NOT_SUPPORTED;
+  if (prec != EVD_FP64 && prec != EVD_SPLIT_BF16) return EVD_ERR_INVALID_ARG;
+  if (n >= (int64_t)1 << 31) return EVD_ERR_INVALID_ARG;
+  if (prec == EVD_SPLIT_BF16 && job != EVD_VECTORS) return EVD_ERR_INVALID_ARG;
+  evd_plan_s* p = new (std::nothrow) evd_plan_s();
+  if (!p) return EVD_ERR_OOM;
+  PlanCore& c = p->core;
+  c.n = n;
+  c.lda = lda;
+  c.job = job;
+  c.prec = prec;
+  c.b = (b > 0) ? b : default_b(n);
+  if (c.b < 2 && b == 0) c.b = 2;
+  c.nb = (nb > 0) ? nb : c.b;
+  c.slices = (prec == EVD_SPLIT_BF16) ? 4 : 8;
+  c.ref_slices = 8;
+  c.refine_iters = (prec == EVD_SPLIT_BF16) ? 2 : 0;
+  c.stream = static_cast<cudaStream_t>(stream);
+  if (const char* s = getenv("EVD_SLICES")) c.slices = atoi(s);
+  cudaGetDevice(&c.device);
+  cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device);
+  if (cudaMalloc(&p->d_status, sizeof(int) * kStatusWords) != cudaSuccess ||
+      cudaMalloc(&p->d_bar, sizeof(unsigned) * 4) != cudaSuccess ||
+      cudaMalloc(&p->d_prog, sizeof(int) * std::max<int64_t>(n, 1)) != cudaSuccess) {
+    cudaFree(p->d_status);
+    cudaFree(p->d_bar);
+    cudaFree(p->d_prog);
+    (void)cudaGetLastError();
+    delete p;
+    return EVD_ERR_OOM;
+  }
+  cudaMemset(p->d_status, 0, sizeof(int) * kStatusWords);
+  cudaMemset(p->d_bar, 0, sizeof(unsigned) * 4);
+  c.status = p->d_status;
+  *plan = p;
+  return EVD_OK;
+}
+
+evd_status_t evd_plan_get_blocking(evd_plan_t p, int* b, int* nb) {
+  if (!p) return EVD_ERR_INVALID_ARG;
+  if (b) *b = p->core.b;
+  if (nb) *nb = p->core.nb;
+  return EVD_OK;
+}
+
+evd_status_t evd_plan_workspace_size(evd_plan_t p, size_t* bytes) {
+  if (!p || !bytes) return EVD_ERR_INVALID_ARG;
+  *bytes = make_layout(p->core, nullptr).total;
+  return EVD_OK;
+}
+
+evd_status_t evd_sbr(evd_plan_t p, double* A, void* ws) {
+  if (!p || (!A && p->core.n > 0)) return EVD_ERR_INVALID_ARG;
+  evd_status_t st = check_ws(p, ws);
+  if (st != EVD_OK) return st;
+  if (p->core.n == 0) return EVD_OK;
+  WsLayout L = make_layout(p->core, ws);
+  st = check_finite_lower(p->core, A, p->core.lda);
+  if (st != EVD_OK) return st;
+  return sbr_run(p->core, A, sbr_work(p, L));
+}
+
+evd_status_t evd_bulge_chase(evd_plan_t p, void* ws, double* d, double* e) {
+  if (!p || ((!d || (!e && p->core.n > 1)) && p->core.n > 0)) return EVD_ERR_INVALID_ARG;
+  evd_status_t st = check_ws(p, ws);
+  if (st != EVD_OK) return st;
+  if (p->core.n == 0) return EVD_OK;
+  WsLayout L = make_layout(p->core, ws);
+  return bc_run(p->core, bc_work(p, L), d, e, p->core.job == EVD_VECTORS);
+}
+
+evd_status_t evd_tridiag_solve(evd_plan_t p, double* d, double* e, double* Qd, int64_t ldq, void* ws) {
+  if (!p || (p->core.n > 0 && !d)) return EVD_ERR_INVALID_ARG;
+  evd_status_t st = check_ws(p, ws);
+  if (st != EVD_OK) return st;
+  const int64_t n = p->core.n;
+  if (n == 0) return EVD_OK;
+  if (n > 1 && !e) return EVD_ERR_INVALID_ARG;
+  WsLayout L = make_layout(p->core, ws);
+  double* Q = Qd;
+  int64_t ld = ldq;
+  if (!Q) {
+    if (!L.Qd_int) return EVD_ERR_INVALID_ARG;  // a vectors plan must be given Qd
+    Q = L.Qd_int;
+    ld = n;
+  } else if (ldq < n) {
+    return EVD_ERR_INVALID_ARG;
+  }
+  return dc_run(p->core, d, e, Q, ld, dc_work(p, L));
+}
+
+evd_status_t evd_back_transform(evd_plan_t p, const double* A_reduced, void* ws, double* Q, int64_t ldq) {
+  if (!p || p->core.job != EVD_VECTORS) return EVD_ERR_INVALID_ARG;
+  const int64_t n = p->core.n;
+  if (n == 0) return EVD_OK;
+  if (!A_reduced || !Q || ldq < n) return EVD_ERR_INVALID_ARG;
+  evd_status_t st = check_ws(p, ws);
+  if (st != EVD_OK) return st;
+  WsLayout L = make_layout(p->core, ws);
+  BackWork bw = back_work(p, L);
+  st = bc_back_run(p->core, bc_work(p, L), Q, ldq, bw);
+  if (st != EVD_OK) return st;
+  return sbr_back_run(p->core, A_reduced, L.sbr_T, L.sbr_tau, Q, ldq, bw);
+}
+
+evd_status_t evd_refine(evd_plan_t p, const double* A0, double* w, double* Q, int64_t ldq, int iterations, void* ws) {
+  if (!p || p->core.prec != EVD_SPLIT_BF16) return EVD_ERR_INVALID_ARG;
+  const int64_t n = p->core.n;
+  if (n == 0) return EVD_OK;
+  if (!A0 || !w || !Q || ldq < n || iterations < 0) return EVD_ERR_INVALID_ARG;
+  evd_status_t st = check_ws(p, ws);
+  if (st != EVD_OK) return st;
+  WsLayout L = make_layout(p->core, ws);
+  return refine_run(p->core, A0, p->core.lda, w, Q, ldq, iterations, refine_work(p, L));
+}
+
+evd_status_t evd_syevd(evd_plan_t p, double* A, double* w, double* Q, int64_t ldq, void* ws) {
+  if (!p) return EVD_ERR_INVALID_ARG;
+  const int64_t n = p->core.n;
+  if (n == 0) return EVD_OK;
+  if (!A || !w) return EVD_ERR_INVALID_ARG;
+  const bool vec = p->core.job == EVD_VECTORS;
+  if (vec && (!Q || ldq < n)) return EVD_ERR_INVALID_ARG;
+  evd_status_t st = check_ws(p, ws);
+  if (st != EVD_OK) return st;
+  WsLayout L = make_layout(p->core, ws);
+  if (p->core.prec == EVD_SPLIT_BF16) {
+    st = copy_matrix(A, p->core.lda, L.A0, n, n, n, p->core.stream);
+    if (st != EVD_OK) return st;
+  }
+  st = evd_sbr(p, A, ws);
+  if (st != EVD_OK) return st;
+  double* etmp = L.e;
+  st = evd_bulge_chase(p, ws, w, etmp);
+  if (st != EVD_OK) return st;
+  st = evd_tridiag_solve(p, w, etmp, vec ? Q : nullptr, ldq, ws);
+  if (st != EVD_OK) return st;
+  if (!vec) return EVD_OK;
+  st = evd_back_transform(p, A, ws, Q, ldq);
+  if (st != EVD_OK) return st;
+  if (p->core.prec == EVD_SPLIT_BF16 && p->core.refine_iters > 0)
+    st = refine_run(p->core, L.A0, n, w, Q, ldq, p->core.refine_iters, refine_work(p, L));
+  return st;
+}
+
+evd_status_t evd_plan_status(evd_plan_t p, int* info) {
+  if (!p) return EVD_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(p->core.stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return EVD_ERR_CUDA;
+  }
+  int h[kStatusWords] = {0};
+  if (cudaMemcpy(h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return EVD_ERR_CUDA;
+  cudaMemset(p->d_status, 0, sizeof(int) * kStatusWords);
+  if (info) *info = h[1];
+  return static_cast<evd_status_t>(h[0]);
+}
+
+void evd_plan_destroy(evd_plan_t p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->core.stream);
+  cudaFree(p->d_status);
+  cudaFree(p->d_bar);
+  cudaFree(p->d_prog);
+  delete p;
+}
+
+// ---------------------------------------------------------------- product engine
+evd_status_t evd_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int slices, size_t* bytes) {
+  if (!bytes || m < 0 || n < 0 || k < 0 || slices < 0 || slices > 8) return EVD_ERR_INVALID_ARG;
+  *bytes = gemm_scratch_bytes(m, n, k, slices);
+  return EVD_OK;
+}
+
+evd_status_t evd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int slices,
+                       void* ws, size_t ws_bytes, void* stream) {
+  transa = (char)toupper(transa);
+  transb = (char)toupper(transb);
+  if ((transa != 'N' && transa != 'T') || (transb != 'N' && transb != 'T')) return EVD_ERR_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 0 || slices < 0 || slices > 8) return EVD_ERR_INVALID_ARG;
+  const int64_t ar = (transa == 'N') ? m : k, br = (transb == 'N') ? k : n;
+  if (lda < std::max<int64_t>(1, ar) || ldb < std::max<int64_t>(1, br) || ldc < std::max<int64_t>(1, m))
+    return EVD_ERR_INVALID_ARG;
+  if (m > 0 && n > 0 && (!C || (k > 0 && (!A || !B)))) return EVD_ERR_INVALID_ARG;
+  if (ws_bytes < gemm_scratch_bytes(m, n, k, slices)) return EVD_ERR_WORKSPACE;
+  Gemm g;
+  g.ta = transa; g.tb = transb; g.m = m; g.n = n; g.k = k; g.alpha = alpha; g.A = A; g.lda = lda;
+  g.B = B; g.ldb = ldb; g.beta = beta; g.C = C; g.ldc = ldc;
+  return gemm(g, slices, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Bulge chasing: band (half-width b) -> symmetric tridiagonal (Sec. 2.1.1, Sec. 4.2).
+//
+// Sweep j (j = 0 .. n-3) reduces column j.  Step k works on the rows
+// R_k = [r0, r1], r0 = j + 1 + k b, r1 = min(r0 + b - 1, n - 1):
+//   * the reflector H = I - tau v v^T (v0 = 1, LAPACK sign choice) annihilates
+//     A(r0+1 : r1, c) with c = j for k = 0 and c = r0 - b (the first column of the
+//     bulge the previous step created) for k >= 1;
+//   * H is applied from the left to the rest of that bulge, A(R_k, c+1 : r0-1),
+//     two-sided to the diagonal block A(R_k, R_k), and from the right to the block
+//     below, A(r1+1 : r1+b, R_k), which creates the next bulge.
+// The band lives in (2b+1) x n lower band storage (room for the bulge) in global
+// memory, which for the sizes of interest stays in the 129 MB L2.
+//
+// Concurrency (the single-GPU form of the pipelined BC): one cooperative launch,
+// CTA g runs sweeps j = g, g + G, ...  Before step k of sweep j it waits (bounded)
+// until sweep j-1 has completed step k+2: the rows and columns step k of sweep j
+// touches are [r0, r1 + b] x [r0 - b, r1], so step k of sweep j and step k' >= k+3
+// of sweep j-1 touch disjoint entries, and every entry sweep j reads has already
+// received all of sweep j-1's updates that precede it in sweep order.
+#include <climits>
+#include <cstdio>
+
+#include "device_util.cuh"
+#include "evd_internal.h"
+
+namespace evd {
+
+namespace {
+
+constexpr int BC_NT = 128;
+constexpr int BC_LAG = 3;  // sweep j step k waits for sweep j-1 to finish step k + BC_LAG - 1
+
+// Number of steps of sweep j: steps with |R_k| >= 2.
+__host__ __device__ inline int64_t sweep_steps(int64_t n, int b, int64_t j) {
+  if (j + 3 > n) return 0;
+  return (n - 3 - j) / b + 1;
+}
+// F(T) = sum_{t=0}^{T} floor(t / b)
+__host__ __device__ inline int64_t floor_sum(int64_t T, int b) {
+  if (T < 0) return 0;
+  int64_t q = T / b;
+  return (int64_t)b * q * (q - 1) / 2 + q * (T - q * b + 1);
+}
+// Index of the first reflector of sweep j (sweeps stored one after another).
+__host__ __device__ inline int64_t sweep_offset(int64_t n, int b, int64_t j) {
+  int64_t jj = j < n - 2 ? j : (n - 2 > 0 ? n - 2 : 0);
+  if (n < 3) return 0;
+  return floor_sum(n - 3, b) - floor_sum(n - 3 - jj, b) + jj;
+}
+
+struct BcArgs {
+  double* band;
+  int64_t n;
+  int b;
+  double* U;      // nullptr when vectors are not wanted
+  double* Utau;
+  int* prog;
+  int* st;
+};
+
+// Band entries are read and written through L2 only (ld.cg / st.cg): other CTAs
+// (other sweeps) update them, and L1 is not coherent across SMs.
+__device__ __forceinline__ double bget(const double* band, int ldb, int64_t r, int64_t c) {
+  return __ldcg(band + (r - c) + c * ldb);
+}
+__device__ __forceinline__ void bput(double* band, int ldb, int64_t r, int64_t c, double x) {
+  __stcg(band + (r - c) + c * ldb, x);
+}
+
+__global__ void __launch_bounds__(BC_NT) k_bulge_chase(const BcArgs a) {
+  __shared__ double v[128];
+  __shared__ double wv[128];
+  __shared__ double red[BC_NT];
+  __shared__ double par[4];
+  const int b = a.b, ldb = 2 * b + 1;
+  const int64_t n = a.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = BC_NT / 32;
+  for (int64_t j = blockIdx.x; j + 3 <= n; j += gridDim.x) {
+    const int64_t K = sweep_steps(n, b, j);
+    const int64_t Kprev = (j > 0) ? sweep_steps(n, b, j - 1) : 0;
+    const int64_t uoff = sweep_offset(n, b, j);
+    for (int64_t k = 0; k < K; ++k) {
+      if (j > 0) {
+        int64_t need = k + BC_LAG;
+        if (need > Kprev) need = Kprev;
+        if (threadIdx.x == 0) {
+          if (!wait_geq(a.prog + (j - 1), (int)need, a.st, (int)(j + 1))) par[3] = 1.0; else par[3] = 0.0;
+        }
+        __syncthreads();
+        if (par[3] != 0.0) return;
+      }
+      const int64_t r0 = j + 1 + k * b;
+      const int64_t r1 = (r0 + b - 1 < n - 1) ? r0 + b - 1 : n - 1;
+      const int m = (int)(r1 - r0 + 1);
+      const int64_t c = (k == 0) ? j : r0 - b;
+      // ---- reflector from x = A(R_k, c)
+      double x = 0.0;
+      if (threadIdx.x < m) x = bget(a.band, ldb, r0 + threadIdx.x, c);
+      double ss = (threadIdx.x >= 1 && threadIdx.x < m) ? x * x : 0.0;
+      ss = block_sum<BC_NT>(ss, red);
+      if (threadIdx.x == 0) {
+        double alpha = x, tau = 0.0, beta = alpha, scale = 0.0;
+        if (ss != 0.0) {
+          double nrm = sqrt(alpha * alpha + ss);
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        par[0] = tau; par[1] = beta; par[2] = scale;
+      }
+      __syncthreads();
+      const double tau = par[0], beta = par[1], scale = par[2];
+      if (threadIdx.x < b) v[threadIdx.x] = (threadIdx.x == 0) ? 1.0 : (threadIdx.x < m ? x * scale : 0.0);
+      __syncthreads();
+      if (a.U) {
+        const int64_t idx = uoff + k;
+        if (threadIdx.x < b) a.U[idx * b + threadIdx.x] = v[threadIdx.x];
+        if (threadIdx.x == 0) a.Utau[idx] = tau;
+      }
+      // annihilated column
+      if (threadIdx.x < m) bput(a.band, ldb, r0 + threadIdx.x, c, (threadIdx.x == 0) ? beta : 0.0);
+      if (tau != 0.0) {
+        // ---- left application to the rest of the bulge: columns c+1 .. r0-1 (k >= 1)
+        for (int64_t cc = c + 1 + warp; cc < r0; cc += nwarps) {
+          double s = 0.0;
+          for (int t = lane; t < m; t += 32) s += v[t] * bget(a.band, ldb, r0 + t, cc);
+          s = warp_sum(s) * tau;
+          for (int t = lane; t < m; t += 32) bput(a.band, ldb, r0 + t, cc, bget(a.band, ldb, r0 + t, cc) - s * v[t]);
+        }
+        // ---- two-sided on the diagonal block D = A(R_k, R_k)
+        for (int p = threadIdx.x; p < m; p += BC_NT) {
+          double s = 0.0;
+          for (int q = 0; q < m; ++q) {
+            double dpq = (p >= q) ? bget(a.band, ldb, r0 + p, r0 + q) : bget(a.band, ldb, r0 + q, r0 + p);
+            s += dpq * v[q];
+          }
+          wv[p] = tau * s;
+        }
+        __syncthreads();
+        double pv = (threadIdx.x < m) ? wv[threadIdx.x] * v[threadIdx.x] : 0.0;
+        pv = block_sum<BC_NT>(pv, red);
+        const double alpha = 0.5 * tau * pv;
+        if (threadIdx.x < m) wv[threadIdx.x] -= alpha * v[threadIdx.x];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < m * m; idx += BC_NT) {
+          int p = idx % m, q = idx / m;
+          if (p >= q) bput(a.band, ldb, r0 + p, r0 + q, bget(a.band, ldb, r0 + p, r0 + q) - (v[p] * wv[q] + wv[p] * v[q]));
+        }
+        // ---- right application to the block below: rows r1+1 .. min(r1+b, n-1)
+        const int64_t rb_end = (r1 + b < n - 1) ? r1 + b : n - 1;
+        for (int64_t r = r1 + 1 + warp; r <= rb_end; r += nwarps) {
+          double s = 0.0;
+          for (int t = lane; t < m; t += 32) s += bget(a.band, ldb, r, r0 + t) * v[t];
+          s = warp_sum(s) * tau;
+          for (int t = lane; t < m; t += 32) bput(a.band, ldb, r, r0 + t, bget(a.band, ldb, r, r0 + t) - s * v[t]);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(a.prog + j, (int)(k + 1));
+      }
+    }
+    if (K == 0 && threadIdx.x == 0) st_release(a.prog + j, 0);
+  }
+}
+
+__global__ void k_extract_tridiag(const double* band, int b, int64_t n, double* d, double* e) {
+  const int ldb = 2 * b + 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    d[i] = band[i * ldb];
+    if (i + 1 < n) e[i] = (b >= 1) ? band[1 + i * ldb] : 0.0;
+  }
+}
+
+}  // namespace
+
+int64_t bc_num_reflectors(int64_t n, int b) {
+  if (n < 3) return 0;
+  return sweep_offset(n, b, n - 2);
+}
+
+evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, bool vectors) {
+  const int64_t n = pc.n;
+  cudaStream_t s = pc.stream;
+  if (n >= 3 && pc.b >= 2) {
+    EVD_CUDA_TRY(cudaMemsetAsync(w.prog, 0, sizeof(int) * n, s));
+    BcArgs a;
+    a.band = w.band; a.n = n; a.b = pc.b;
+    a.U = vectors ? w.U : nullptr;
+    a.Utau = w.Utau;
+    a.prog = w.prog; a.st = pc.status;
+    int maxG = max_coresident_blocks((const void*)k_bulge_chase, BC_NT, 0);
+    int64_t G = n - 2;
+    if (G > maxG) G = maxG;
+    void* args[] = {&a};
+    EVD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bulge_chase, dim3((unsigned)G), dim3(BC_NT), args, 0, s));
+  }
+  if (n > 0) {
+    k_extract_tridiag<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(w.band, pc.b, n, d, e);
+    EVD_CUDA_TRY(cudaGetLastError());
+  }
+  return EVD_OK;
+}
+
+}  // namespace evd

@@ -1,0 +1,120 @@
+// Dense products C = alpha op(A) op(B) + beta C in FP64.
+//
+// Two engines:
+//  * a plain FP64 CUDA-core kernel (slices == 0), used for small or thin shapes;
+//  * the tensor-core split product (slices 1..8, evd_ozaki.cu), used for the large
+//    contractions of SBR (Eq. 1), the back transformation and the D&C merges.
+#include <cstdio>
+
+#include "device_util.cuh"
+#include "evd_internal.h"
+#include "evd_ozaki.h"
+
+namespace evd {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__device__ __forceinline__ double load_a(const Gemm& g, int64_t r, int64_t c) {
+  // op(A)(r, c), 0 <= r < m, 0 <= c < k
+  if (g.a_sym_lower) return (r >= c) ? g.A[r + c * g.lda] : g.A[c + r * g.lda];
+  return (g.ta == 'N') ? g.A[r + c * g.lda] : g.A[c + r * g.lda];
+}
+__device__ __forceinline__ double load_b(const Gemm& g, int64_t r, int64_t c) {
+  // op(B)(r, c), 0 <= r < k, 0 <= c < n
+  return (g.tb == 'N') ? g.B[r + c * g.ldb] : g.B[c + r * g.ldb];
+}
+
+__global__ void __launch_bounds__(NT) k_dgemm_simt(const Gemm g) {
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  if (g.lower && n0 > m0 + BM - 1) return;  // tile strictly above the diagonal
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int64_t k0 = 0; k0 < g.k; k0 += BK) {
+    // A tile: 64 x 16
+    for (int t = threadIdx.x; t < BM * BK; t += NT) {
+      int i, kk;
+      if (g.ta == 'N' || g.a_sym_lower) { i = t % BM; kk = t / BM; }
+      else { kk = t % BK; i = t / BK; }
+      int64_t r = m0 + i, c = k0 + kk;
+      As[kk][i] = (r < g.m && c < g.k) ? load_a(g, r, c) : 0.0;
+    }
+    for (int t = threadIdx.x; t < BN * BK; t += NT) {
+      int j, kk;
+      if (g.tb == 'N') { kk = t % BK; j = t / BK; }
+      else { j = t % BN; kk = t / BN; }
+      int64_t r = k0 + kk, c = n0 + j;
+      Bs[kk][j] = (r < g.k && c < g.n) ? load_b(g, r, c) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t r = m0 + tx + 16 * i, c = n0 + ty + 16 * j;
+      if (r < g.m && c < g.n && (!g.lower || r >= c)) {
+        double* p = g.C + r + c * g.ldc;
+        double v = g.alpha * acc[i][j];
+        if (g.beta != 0.0) v = fma(g.beta, *p, v);
+        *p = v;
+      }
+    }
+}
+
+__global__ void k_scale(double* C, int64_t ldc, int64_t m, int64_t n, double beta, bool lower) {
+  int64_t j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (lower && i < j) continue;
+    double* p = C + i + j * ldc;
+    *p = (beta == 0.0) ? 0.0 : beta * *p;
+  }
+}
+
+}  // namespace
+
+size_t gemm_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
+  if (slices <= 0) return 0;
+  return ozaki_scratch_bytes(m, n, k, slices);
+}
+
+evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes, cudaStream_t s) {
+  if (g.m <= 0 || g.n <= 0) return EVD_OK;
+  if (g.k <= 0 || g.alpha == 0.0) {
+    if (g.beta == 1.0) return EVD_OK;
+    for (int64_t j0 = 0; j0 < g.n; j0 += 65535) {
+      int64_t cols = g.n - j0 < 65535 ? g.n - j0 : 65535;
+      k_scale<<<dim3(4, (unsigned)cols), 256, 0, s>>>(g.C + j0 * g.ldc, g.ldc, g.m, cols, g.beta, false);
+    }
+    EVD_CUDA_TRY(cudaGetLastError());
+    return EVD_OK;
+  }
+  if (slices > 0 && ozaki_eligible(g)) return ozaki_gemm(g, slices, scratch, scratch_bytes, s);
+  dim3 grid((unsigned)ceil_div(g.m, BM), (unsigned)ceil_div(g.n, BN));
+  if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
+  k_dgemm_simt<<<grid, NT, 0, s>>>(g);
+  EVD_CUDA_TRY(cudaGetLastError());
+  return EVD_OK;
+}
+
+}  // namespace evd

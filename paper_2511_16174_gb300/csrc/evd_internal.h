@@ -1,0 +1,165 @@
+// Internal declarations shared by the CUDA translation units of libevd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "evd.h"
+
+namespace evd {
+
+// ---------------------------------------------------------------- status word
+// Device status word layout (int[8]): [0] status code (evd_status_t), [1] info,
+// [2] abort flag for cooperative kernels, [3..7] reserved.
+constexpr int kStatusWords = 8;
+
+// Spin limit for every device-side wait (a wait on a flag written by another CTA
+// of the same launch).  Each iteration sleeps ~256 ns, so the limit is a few
+// seconds of wall time.
+constexpr long long kSpinLimit = 16ll * 1000 * 1000;
+
+#define EVD_CUDA_TRY(expr)                                    \
+  do {                                                        \
+    cudaError_t e__ = (expr);                                 \
+    if (e__ != cudaSuccess) return ::evd::cuda_fail(e__, #expr); \
+  } while (0)
+
+evd_status_t cuda_fail(cudaError_t e, const char* what);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- workspace
+// A bump allocator over the caller's workspace.  Sizes are computed by running the
+// same carve sequence with base == nullptr.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// ---------------------------------------------------------------- products
+// C = alpha op(A) op(B) + beta C (column-major FP64).  `lower` restricts the
+// computed and written part of C to i >= j (C square).  `slices` = 0: FP64 CUDA
+// cores; 1..8: tensor-core split product with that many slices.
+struct Gemm {
+  char ta = 'N', tb = 'N';
+  int64_t m = 0, n = 0, k = 0;
+  double alpha = 1.0;
+  const double* A = nullptr;
+  int64_t lda = 1;
+  const double* B = nullptr;
+  int64_t ldb = 1;
+  double beta = 0.0;
+  double* C = nullptr;
+  int64_t ldc = 1;
+  bool lower = false;
+  // A is symmetric with only its lower triangle stored (op(A) = A, m == k).
+  bool a_sym_lower = false;
+};
+
+// Scratch a product needs (bytes) and the call itself.
+size_t gemm_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices);
+evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes, cudaStream_t s);
+
+// ---------------------------------------------------------------- the plan
+
+
+struct PlanCore {
+  int64_t n = 0, lda = 0;
+  evd_job_t job = EVD_VALUES;
+  evd_prec_t prec = EVD_FP64;
+  int b = 32, nb = 32;
+  int slices = 8;         // slices for SBR / back transform / merges
+  int ref_slices = 8;     // slices for refinement residual products
+  int refine_iters = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+  int* status = nullptr;  // device int[kStatusWords]
+};
+
+// Stage entry points (each enqueues on core.stream).
+struct SbrWork {
+  double* tau;     // n
+  double* T;       // npanels * b * b   (T factor of each panel, column-major b x b)
+  double* V;       // n * nb            (explicit V of the current panel block)
+  double* W;       // n * nb
+  double* Z;       // n * nb
+  double* Y;       // n * nb            (scratch, A2 W)
+  double* M;       // nb * nb * 4       (small products)
+  double* partial; // per-CTA partial sums of the panel kernel
+  unsigned* bar;   // grid barrier words
+  double* band;    // (2b+1) x n lower band with room for the bulge
+  void* gemm_ws;
+  size_t gemm_ws_bytes;
+};
+evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w);
+
+struct BcWork {
+  double* band;    // (2b+1) x n
+  double* U;       // reflectors, b doubles each (v[0] = 1 explicit)
+  double* Utau;    // one tau per reflector
+  int64_t* off;    // n+1 prefix offsets of each sweep's reflectors
+  int* prog;       // n progress counters
+  unsigned* bar;
+};
+int64_t bc_num_reflectors(int64_t n, int b);
+evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, bool vectors);
+
+struct DcWork {
+  double* Qtmp;    // n x n (block columns gathered in pole order, rotated)
+  double* Qn;      // n x n (nondeflated columns; then the assembled block)
+  double* Umat;    // n x n (secular eigenvectors of the merges)
+  double* vec;     // 10 n doubles
+  int* ivec;       // 32 n ints (8 n index arrays + merge descriptors)
+  void* gemm_ws;
+  size_t gemm_ws_bytes;
+};
+evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t ldq,
+                    const DcWork& w);
+
+struct BackWork {
+  double* Tg;      // T factors of the BC reflector groups
+  double* Vp;      // explicit V of an SBR panel block (n x nb)
+  double* Wp;      // nb x n
+  double* Tp;      // nb x nb
+  void* gemm_ws;
+  size_t gemm_ws_bytes;
+};
+evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq,
+                         const BackWork& w);
+evd_status_t sbr_back_run(const PlanCore& pc, const double* A, const double* sbr_T,
+                          const double* sbr_tau, double* Q, int64_t ldq, const BackWork& w);
+
+// Refinement (Ogita-Aishima)
+struct RefineWork {
+  double* R;   // n x n
+  double* S;   // n x n
+  double* AX;  // n x n
+  double* E;   // n x n
+  double* vec; // 4 n
+  void* gemm_ws;
+  size_t gemm_ws_bytes;
+};
+evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, double* w, double* Q,
+                        int64_t ldq, int iters, const RefineWork& rw);
+
+// Small helpers (evd_util.cu)
+evd_status_t check_finite_lower(const PlanCore& pc, const double* A, int64_t lda);
+evd_status_t copy_lower_to_full(const double* A, int64_t lda, double* B, int64_t ldb, int64_t n,
+                                cudaStream_t s);
+evd_status_t copy_matrix(const double* A, int64_t lda, double* B, int64_t ldb, int64_t m, int64_t n,
+                         cudaStream_t s);
+evd_status_t set_identity(double* Q, int64_t ldq, int64_t n, cudaStream_t s);
+int max_coresident_blocks(const void* kernel, int threads, size_t smem);
+
+}  // namespace evd

@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark: dense symmetric EVD (eigenvalues + eigenvectors) on GB300.
+
+One step = one whole solve A -> (Lambda, Q) through the C ABI: SBR (panel QR + Eq. 1
+trailing update), bulge chasing, divide and conquer, back transformation, on a
+synthetic A = Q Lambda Q^T with a known spectrum.  The metric is effective TFLOP/s
+with the tridiagonalization counted as 4n^3/3 and the back transformation as 2n^3;
+seconds per solve are in the JSON line too.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--n N] [--prec fp64|split_bf16]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Multi-GPU: one process per GPU (torchrun); the single-matrix EVD does not shard, so
+each rank solves its own replica ("replicas only") and the value is the whole-job
+throughput, timed as the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "n=49152 EVD seconds & effective TFLOPS; split-precision vs FP64 at equal residual"
+DEFAULT_N = 8192
+FP64_ALU_PEAK_TFLOPS = 1.25  # FP64 (CUDA-core and DMMA) nominal rate of GB300
+
+
+def nominal_flops(n):
+    return 4.0 * n ** 3 / 3.0 + 2.0 * n ** 3
+
+
+def workload_name(n, prec):
+    spec = "geometric 1..1e-8 random signs" if n <= 8192 else "uniform [-1,1]"
+    return (f"n={n} {'FP64' if prec == 'fp64' else 'split-BF16+refinement'} EVD with eigenvectors, "
+            f"A=Q Lambda Q^T, Q = 32 seeded Householder reflectors, Lambda {spec}")
+
+
+def spectrum_for(n, seed):
+    from paper_2511_16174_gb300 import inputs
+    if n <= 8192:
+        return inputs.spectrum_geometric(n, seed)
+    return inputs.spectrum_uniform(n, seed)
+
+
+def load_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2511_16174_gb300" / "csrc").glob("*")):
+        h.update(f.name.encode())
+        h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel_cat, n):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current
+    sources and workload (else None)."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    try:
+        d = json.loads(p.read_text())
+    except Exception:
+        return None
+    if d.get("csrc_hash") != csrc_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel_cat)
+    if not ent or ent.get("n") != n:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGINT)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in Path(self.path).read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_oracle_sample(target_s=15.0):
+    """Time the CPU oracle (one-stage tridiagonalization + implicit QL with
+    vectors) on a bounded sample; returns (tflops, n_sample, seconds, cores)."""
+    import oracle
+    from paper_2511_16174_gb300 import inputs
+    n0 = 768
+    A = inputs.goe(n0, 1)
+    t = time.perf_counter()
+    oracle.eigh(A, want_vectors=True)
+    t0 = time.perf_counter() - t
+    ns = int(n0 * (target_s / max(t0, 1e-3)) ** (1.0 / 3.0))
+    ns = max(512, min(4096, ns // 64 * 64))
+    A = inputs.goe(ns, 2)
+    t = time.perf_counter()
+    oracle.eigh(A, want_vectors=True)
+    ts = time.perf_counter() - t
+    return nominal_flops(ns) / ts / 1e12, ns, ts, oracle.num_threads()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    n = args.n
+    vals, times = [], []
+    for i in range(args.warmup + args.steps):
+        tf, ns, ts, cores = run_oracle_sample(target_s=min(20.0, 120.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            vals.append(tf)
+            times.append(ts)
+    v = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(n, args.prec), "n": n, "job": "V", "prec": args.prec},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one-stage Householder + implicit QL with vectors at n={ns} (GOE input), "
+                                   f"{float(np.mean(times)):.1f} s per solve; flops counted as 4n^3/3+2n^3"},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws_, rank, local = dist_setup()
+    if ws_ > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2511_16174_gb300 import evd, inputs
+
+    n = args.n
+    seed = inputs.SEED_BASE + (2 if n > 8192 else 1)
+    lam = np.sort(spectrum_for(n, seed))
+    if n <= 8192:
+        A0 = evd.as_colmajor(torch.from_numpy(inputs.qlq(lam, seed)).cuda())
+    else:
+        A0 = evd.as_colmajor(inputs.qlq_device(lam, seed))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    plan = evd.Plan(n, job="V", prec=args.prec, b=args.b, nb=args.nb, stream=stream)
+    ws = plan.workspace()
+    Aw = evd.empty_colmajor(n, n)
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    Q = evd.empty_colmajor(n, n)
+
+    def step():
+        Aw.copy_(A0)
+        plan.syevd(Aw, w, Q, ws)
+
+    for i in range(args.warmup):
+        step()
+        if i == 0:
+            plan.check("warmup solve")
+    torch.cuda.synchronize()
+    if ws_ > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evd.stats_reset()
+    evd.stats_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if ws_ > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws_ > 1:
+        dist.barrier()
+    evd.stats_enable(False)
+    launches = evd.launch_count()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    plan.check("timed solves")
+    st = evd.stats()
+    if ws_ > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nominal_flops(n) / (ms / 1e3) / 1e12 * ws_
+
+    # ---- accuracy of the last timed result (sampled columns at large n)
+    with torch.no_grad():
+        lam_t = torch.from_numpy(lam).cuda()
+        dlam = float((w - lam_t).abs().max().item())
+        cols = torch.arange(n, device="cuda") if n <= 8192 else torch.randperm(n, device="cuda")[:256]
+        Qs = Q[:, cols]
+        A0s = A0
+        R = A0s @ Qs - Qs * w[cols][None, :]
+        O = Q.t() @ Qs
+        O[cols, torch.arange(len(cols), device="cuda")] -= 1.0
+        normA = float(torch.linalg.matrix_norm(A0).item())
+        resid = float(torch.linalg.matrix_norm(R).item()) / (n * normA) * (n / len(cols)) ** 0.5
+        orth = float(O.abs().max().item())
+    U = 2.0 ** -53
+    acc = {"dlam": dlam, "dlam_bound": 10 * n * U * float(np.max(np.abs(lam))), "orth_max": orth,
+           "orth_bound": 10 * n * U, "resid": resid, "resid_bound": 10 * U,
+           "columns_checked": int(len(cols))}
+
+    # ---- roofline of the dominant kernel category
+    peaks, peak_kind = load_peaks()
+    dom = max(st.items(), key=lambda kv: kv[1][0]) if st else None
+    roof = None
+    if dom:
+        cat, (dms, dfl, dby, dca) = dom
+        per_launch_ms = dms / max(dca, 1)
+        traffic = committed_traffic(cat, n)
+        if cat.startswith("gemm_tc"):
+            pairs = st.get("_pairs", None)
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            roof = {"kernel": cat, "bound": "tensor", "achieved": dfl / (dms / 1e3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "traffic": traffic}
+        elif cat == "bc_chase":
+            peak = peaks.get("hbm_gbs")
+            roof = {"kernel": cat, "bound": "hbm", "achieved": dby / (dms / 1e3) / 1e9, "peak": peak,
+                    "unit": "GB/s", "traffic": traffic}
+        else:
+            roof = {"kernel": cat, "bound": "alu", "achieved": dfl / (dms / 1e3) / 1e12,
+                    "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": traffic}
+        roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+        roof["peak_source"] = (f"{peak_kind} MEASURED_PEAKS.json" if roof["bound"] != "alu"
+                               else "GB300 nominal FP64 rate (1.25 TFLOP/s)")
+        roof["launches"] = int(dca)
+        roof["ms_per_launch"] = per_launch_ms
+        roof["share_of_step"] = dms / (ms * args.steps) if ms > 0 else None
+    breakdown = {k: {"ms": v[0] / args.steps, "calls": v[3] // max(args.steps, 1)} for k, v in st.items()}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Ah.copy_(A0.t())  # A is symmetric: the row-major copy holds the same values
+        wh = torch.empty(n, dtype=torch.float64).pin_memory()
+        Qh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Aw_rm = Aw.t()  # row-major view of the column-major buffer
+
+        def e2e_step():
+            Aw_rm.copy_(Ah, non_blocking=True)
+            plan.syevd(Aw, w, Q, ws)
+            wh.copy_(w, non_blocking=True)
+            Qh.copy_(Q.t(), non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1) / args.steps
+        e2e = {"value": nominal_flops(n) / (ems / 1e3) / 1e12 * ws_, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n + 8 * n * n,
+               "ms_per_step": ems}
+
+    cpu = None
+    if rank == 0 and ws_ == 1 and not args.no_cpu:
+        tf, ns, ts, cores = run_oracle_sample()
+        cpu = {"value": tf, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"one-stage Householder + implicit QL with vectors at n={ns} (GOE input), {ts:.1f} s; "
+                         f"flops counted as 4n^3/3+2n^3"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws_, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(n, args.prec), "n": n, "job": "V", "prec": args.prec,
+                       "b": plan.b, "nb": plan.nb, "seconds_per_solve": ms / 1e3,
+                       "paper_tflops_4n3": 4.0 * n ** 3 / (ms / 1e3) / 1e12,
+                       "l2": "inputs larger than L2 (A is 8 n^2 bytes)", "parallelism": f"replicas{ws_}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "accuracy": acc, "stages": breakdown,
+        }
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=DEFAULT_N)
+    ap.add_argument("--prec", choices=["fp64", "split_bf16"], default="fp64")
+    ap.add_argument("--b", type=int, default=0)
+    ap.add_argument("--nb", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

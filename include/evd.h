@@ -158,6 +158,24 @@ evd_status_t evd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k
 evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char* cache_path,
                           int* b, int* nb);
 
+/* ---------------------------------------------------------------------------
+ * Instrumentation (off by default; used by the benchmark).  When enabled, the
+ * library records CUDA events around its launches on the launching stream,
+ * grouped by category ("gemm_fp64_simt", "gemm_tc_split", "sbr_panel_qr",
+ * "bc_chase", "dc_leaf", "dc_merge", "dc_secular", "bc_back", ...), together with
+ * the algorithmic flops and bytes of each call.  The library also counts every
+ * kernel it launches.  Host-side state, process-wide; not thread-safe across
+ * concurrent solves that query it. */
+void evd_stats_enable(int on);
+void evd_stats_reset(void);
+/* Number of kernels launched since the last evd_stats_reset(). */
+int64_t evd_launch_count(void);
+/* Category names separated by '\n' into buf (capacity cap bytes); returns the count. */
+int evd_stats_categories(char* buf, int cap);
+/* Device milliseconds (sum over calls, synchronizes the events), algorithmic flops
+ * and bytes, and number of calls of one category. */
+evd_status_t evd_stats_query(const char* category, double* ms, double* flops, double* bytes, int64_t* calls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,7 +96,8 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   const int64_t n = pc.n;
   if (n < 3 || pc.b < 2) return EVD_OK;
   const unsigned grid = (unsigned)ceil_div(n, BB_NC);
-  k_bc_back<<<grid, BB_NT, 0, pc.stream>>>(bw.U, bw.Utau, n, pc.b, pc.b, Q, ldq);
+  StatScope sc("bc_back", pc.stream, 4.0 * pc.b * (double)n * (double)bc_num_reflectors(n, pc.b));
+  k_bc_back<<<grid, BB_NT, 0, pc.stream>>>(bw.U, bw.Utau, n, pc.b, pc.b, Q, ldq); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   return EVD_OK;
 }
@@ -115,7 +116,7 @@ evd_status_t sbr_back_run(const PlanCore& pc, const double* A, const double* sbr
     const int bw = (int)((n - c0 < b) ? n - c0 : b);
     const int kb = (int)((bw < m) ? bw : m);
     k_explicit_v<<<dim3((unsigned)std::min<int64_t>(ceil_div(m, 256), 64), (unsigned)kb), 256, 0, s>>>(
-        A, lda, r0, c0, m, kb, w.Vp, n);
+        A, lda, r0, c0, m, kb, w.Vp, n); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
     // Wp = V^T X(r0:, :)   (kb x n)
     Gemm g1;

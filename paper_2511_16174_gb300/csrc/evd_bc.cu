@@ -194,10 +194,13 @@ evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, b
     int64_t G = n - 2;
     if (G > maxG) G = maxG;
     void* args[] = {&a};
-    EVD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bulge_chase, dim3((unsigned)G), dim3(BC_NT), args, 0, s));
+    // model bytes (each step reads and writes its 2b x b window; U written once)
+    const double nn = (double)n * (double)n;
+    StatScope sc("bc_chase", s, 5.0 * pc.b * nn, 16.0 * pc.b * nn + (vectors ? 4.0 * nn : 0.0));
+    EVD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bulge_chase, dim3((unsigned)G), dim3(BC_NT), args, 0, s)); count_launch();
   }
   if (n > 0) {
-    k_extract_tridiag<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(w.band, pc.b, n, d, e);
+    k_extract_tridiag<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(w.band, pc.b, n, d, e); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
   }
   return EVD_OK;

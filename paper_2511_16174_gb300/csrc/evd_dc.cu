@@ -522,11 +522,14 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
   // Q = 0, tears, leaves
   for (int64_t j0 = 0; j0 < n; j0 += 65535) {
     int64_t cols = n - j0 < 65535 ? n - j0 : 65535;
-    k_zero_cols<<<dim3(4, (unsigned)cols), 256, 0, s>>>(Q, ldq, n, j0);
+    k_zero_cols<<<dim3(4, (unsigned)cols), 256, 0, s>>>(Q, ldq, n, j0); count_launch();
   }
-  if (nmerge) k_dc_tear<<<(unsigned)ceil_div(nmerge, 128), 128, 0, s>>>(d_md, (int)nmerge, d, e);
-  k_dc_leaf<<<(unsigned)ceil_div(nleaves * 32, 128), 128, 0, s>>>(d_loff, d_ln, (int)nleaves, d, e, Q, ldq,
-                                                                   pc.status);
+  if (nmerge) k_dc_tear<<<(unsigned)ceil_div(nmerge, 128), 128, 0, s>>>(d_md, (int)nmerge, d, e); count_launch();
+  {
+    StatScope sc_leaf("dc_leaf", s);
+    k_dc_leaf<<<(unsigned)ceil_div(nleaves * 32, 128), 128, 0, s>>>(d_loff, d_ln, (int)nleaves, d, e, Q, ldq,
+                                                                     pc.status); count_launch();
+  }
   EVD_CUDA_TRY(cudaGetLastError());
   std::vector<int> hk(nmerge + 1);
   for (size_t L = 0; L + 1 < lvl_start.size(); ++L) {
@@ -536,13 +539,15 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
     int64_t mmax = 0;
     for (size_t q = 0; q < cnt; ++q) mmax = std::max<int64_t>(mmax, all[b0 + q].n1 + all[b0 + q].n2);
     const unsigned rx = (unsigned)std::min<int64_t>(ceil_div(mmax, 256), 8);
-    k_dc_prepare<<<(unsigned)cnt, 256, 0, s>>>(md, d, e, Q, ldq, ds, zs, perm, d_rho + b0, d_tol + b0);
+    { StatScope sc("dc_merge", s);
+    k_dc_prepare<<<(unsigned)cnt, 256, 0, s>>>(md, d, e, Q, ldq, ds, zs, perm, d_rho + b0, d_tol + b0); count_launch();
     k_dc_deflate<<<(unsigned)ceil_div(cnt, 64), 64, 0, s>>>(md, (int)cnt, ds, zs, d_rho + b0, d_tol + b0, ndl, dfl,
-                                                            rotp, rotj, rotc, rots, d_k + b0, d_nrot + b0);
-    k_dc_gather<<<dim3(rx, (unsigned)mmax, (unsigned)cnt), 256, 0, s>>>(md, perm, Q, ldq, w.Qtmp, n);
+                                                            rotp, rotj, rotc, rots, d_k + b0, d_nrot + b0); count_launch();
+    k_dc_gather<<<dim3(rx, (unsigned)mmax, (unsigned)cnt), 256, 0, s>>>(md, perm, Q, ldq, w.Qtmp, n); count_launch();
     k_dc_rotate<<<dim3((unsigned)ceil_div(mmax, 128), (unsigned)cnt), 128, 0, s>>>(md, d_nrot + b0, rotp, rotj, rotc,
-                                                                                 rots, w.Qtmp, n);
+                                                                                 rots, w.Qtmp, n); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
+    }
     // the number of nondeflated roots sizes the products: read it on the host
     EVD_CUDA_TRY(cudaMemcpyAsync(hk.data(), d_k + b0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
     EVD_CUDA_TRY(cudaStreamSynchronize(s));
@@ -550,12 +555,14 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
     for (size_t q = 0; q < cnt; ++q) kmax = std::max(kmax, hk[q]);
     if (kmax > 0) {
       k_dc_gather_nd<<<dim3(rx, (unsigned)kmax, (unsigned)cnt), 256, 0, s>>>(md, d_k + b0, ndl, ds, zs, dl, zl,
-                                                                             w.Qtmp, n, w.Qn);
+                                                                             w.Qtmp, n, w.Qn); count_launch();
       const unsigned kx = (unsigned)ceil_div(kmax, 128);
-      k_dc_secular<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, zl, d_rho + b0, org, tau, pc.status);
-      k_dc_lowner<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, zl, d_rho + b0, org, tau, zh);
-      k_dc_vectors<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, org, tau, zh, w.Umat, n);
+      { StatScope sc("dc_secular", s);
+      k_dc_secular<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, zl, d_rho + b0, org, tau, pc.status); count_launch();
+      k_dc_lowner<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, zl, d_rho + b0, org, tau, zh); count_launch();
+      k_dc_vectors<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, org, tau, zh, w.Umat, n); count_launch();
       EVD_CUDA_TRY(cudaGetLastError());
+      }
       // X = Qn U into the first k columns of the block of Q (the block is free now)
       for (size_t q = 0; q < cnt; ++q) {
         const int k = hk[q];
@@ -572,11 +579,12 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
         if (st != EVD_OK) return st;
       }
     }
+    StatScope sc2("dc_merge", s);
     k_dc_rank<<<dim3((unsigned)ceil_div(mmax, 128), (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, org, tau, ds, dfl,
-                                                                               vals, rank);
+                                                                               vals, rank); count_launch();
     k_dc_assemble<<<dim3(rx, (unsigned)mmax, (unsigned)cnt), 256, 0, s>>>(md, d_k + b0, rank, dfl, Q, ldq, w.Qtmp, n,
-                                                                          w.Qn);
-    k_dc_copy_back<<<dim3(rx, (unsigned)mmax, (unsigned)cnt), 256, 0, s>>>(md, vals, d, w.Qn, n, Q, ldq);
+                                                                          w.Qn); count_launch();
+    k_dc_copy_back<<<dim3(rx, (unsigned)mmax, (unsigned)cnt), 256, 0, s>>>(md, vals, d, w.Qn, n, Q, ldq); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
   }
   return EVD_OK;

@@ -104,7 +104,7 @@ evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes
     if (g.beta == 1.0) return EVD_OK;
     for (int64_t j0 = 0; j0 < g.n; j0 += 65535) {
       int64_t cols = g.n - j0 < 65535 ? g.n - j0 : 65535;
-      k_scale<<<dim3(4, (unsigned)cols), 256, 0, s>>>(g.C + j0 * g.ldc, g.ldc, g.m, cols, g.beta, false);
+      k_scale<<<dim3(4, (unsigned)cols), 256, 0, s>>>(g.C + j0 * g.ldc, g.ldc, g.m, cols, g.beta, false); count_launch();
     }
     EVD_CUDA_TRY(cudaGetLastError());
     return EVD_OK;
@@ -112,7 +112,9 @@ evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes
   if (slices > 0 && ozaki_eligible(g)) return ozaki_gemm(g, slices, scratch, scratch_bytes, s);
   dim3 grid((unsigned)ceil_div(g.m, BM), (unsigned)ceil_div(g.n, BN));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
-  k_dgemm_simt<<<grid, NT, 0, s>>>(g);
+  const double flops = (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;
+  StatScope sc("gemm_fp64_simt", s, flops);
+  k_dgemm_simt<<<grid, NT, 0, s>>>(g); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   return EVD_OK;
 }

@@ -153,6 +153,24 @@ struct RefineWork {
 evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, double* w, double* Q,
                         int64_t ldq, int iters, const RefineWork& rw);
 
+// ---------------------------------------------------------------- stats (evd_stats.cu)
+// RAII scope: when stats are enabled, records CUDA events around the enclosed
+// launches on stream s under category `cat` and adds the algorithmic flops/bytes.
+class StatScope {
+ public:
+  StatScope(const char* cat, cudaStream_t s, double flops = 0, double bytes = 0);
+  ~StatScope();
+  StatScope(const StatScope&) = delete;
+  StatScope& operator=(const StatScope&) = delete;
+
+ private:
+  const char* cat_;
+  cudaStream_t s_;
+  void* a_ = nullptr;
+  bool on_ = false;
+};
+void count_launch(int n = 1);
+
 // Small helpers (evd_util.cu)
 evd_status_t check_finite_lower(const PlanCore& pc, const double* A, int64_t lda);
 evd_status_t copy_lower_to_full(const double* A, int64_t lda, double* B, int64_t ldb, int64_t n,

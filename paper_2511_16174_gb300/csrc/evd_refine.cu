@@ -106,8 +106,8 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
   double* part = rw.vec + n;       // n partials
   double* lam = rw.vec;
   const unsigned rx = (unsigned)std::min<int64_t>(ceil_div(n, 256), 16);
-  k_sumsq_partial<<<(unsigned)n, 256, 0, s>>>(A0, lda0, n, 1, nullptr, part);
-  k_sum_final<<<1, 256, 0, s>>>(part, n, norms + 0);
+  k_sumsq_partial<<<(unsigned)n, 256, 0, s>>>(A0, lda0, n, 1, nullptr, part); count_launch();
+  k_sum_final<<<1, 256, 0, s>>>(part, n, norms + 0); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   for (int it = 0; it < iters; ++it) {
     // R = I - X^T X
@@ -116,7 +116,7 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
     g1.C = rw.R; g1.ldc = n; g1.alpha = -1.0; g1.beta = 0.0;
     evd_status_t st = gemm(g1, pc.ref_slices, rw.gemm_ws, rw.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
-    k_add_identity<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(rw.R, n, n);
+    k_add_identity<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(rw.R, n, n); count_launch();
     // AX = A0 X (A0 symmetric, lower stored)
     Gemm g2;
     g2.m = n; g2.n = n; g2.k = n; g2.A = A0; g2.lda = lda0; g2.a_sym_lower = true; g2.B = Q; g2.ldb = ldq;
@@ -129,12 +129,12 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
     g3.C = rw.S; g3.ldc = n; g3.alpha = 1.0; g3.beta = 0.0;
     st = gemm(g3, pc.ref_slices, rw.gemm_ws, rw.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
-    k_lambda<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(rw.S, rw.R, n, n, lam);
-    k_sumsq_partial<<<(unsigned)n, 256, 0, s>>>(rw.R, n, n, 0, nullptr, part);
-    k_sum_final<<<1, 256, 0, s>>>(part, n, norms + 1);
-    k_sumsq_partial<<<(unsigned)n, 256, 0, s>>>(rw.S, n, n, 2, lam, part);
-    k_sum_final<<<1, 256, 0, s>>>(part, n, norms + 2);
-    k_form_E<<<dim3(rx, (unsigned)n), 256, 0, s>>>(rw.S, rw.R, n, n, lam, norms);
+    k_lambda<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(rw.S, rw.R, n, n, lam); count_launch();
+    k_sumsq_partial<<<(unsigned)n, 256, 0, s>>>(rw.R, n, n, 0, nullptr, part); count_launch();
+    k_sum_final<<<1, 256, 0, s>>>(part, n, norms + 1); count_launch();
+    k_sumsq_partial<<<(unsigned)n, 256, 0, s>>>(rw.S, n, n, 2, lam, part); count_launch();
+    k_sum_final<<<1, 256, 0, s>>>(part, n, norms + 2); count_launch();
+    k_form_E<<<dim3(rx, (unsigned)n), 256, 0, s>>>(rw.S, rw.R, n, n, lam, norms); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
     // X <- X + X E   (product into AX, then add)
     Gemm g4;
@@ -142,7 +142,7 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
     g4.C = rw.AX; g4.ldc = n; g4.alpha = 1.0; g4.beta = 0.0;
     st = gemm(g4, pc.ref_slices, rw.gemm_ws, rw.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
-    k_axpy_mat<<<dim3(rx, (unsigned)n), 256, 0, s>>>(rw.AX, n, Q, ldq, n);
+    k_axpy_mat<<<dim3(rx, (unsigned)n), 256, 0, s>>>(rw.AX, n, Q, ldq, n); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
   }
   EVD_CUDA_TRY(cudaMemcpyAsync(w, lam, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));

@@ -223,7 +223,8 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
     if (G < 1) G = 1;
     EVD_CUDA_TRY(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
     void* args[] = {&pa};
-    EVD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PQ_NT), args, 0, s));
+    StatScope sc("sbr_panel_qr", s, 4.0 * (double)m * bw * bw);
+    EVD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PQ_NT), args, 0, s)); count_launch();
     // ---- Eq. 1: Y = A2 W ; M = W^T Y ; Z = Y - 1/2 V M ; A2 -= V Z^T + Z V^T
     double* A2 = A + r0 + r0 * lda;
     Gemm g1;
@@ -253,13 +254,13 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
     st = gemm(g5, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
     // ---- band of this column block is final
-    k_pack_band<<<bw, 128, 0, s>>>(A, lda, n, b, w.band, c0, c0 + bw, c0, 1);
+    k_pack_band<<<bw, 128, 0, s>>>(A, lda, n, b, w.band, c0, c0 + bw, c0, 1); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
   }
   // remaining columns need no reduction
   const int64_t cstart = p * b;
   if (cstart < n) {
-    k_pack_band<<<(unsigned)(n - cstart), 128, 0, s>>>(A, lda, n, b, w.band, cstart, n, cstart, 0);
+    k_pack_band<<<(unsigned)(n - cstart), 128, 0, s>>>(A, lda, n, b, w.band, cstart, n, cstart, 0); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
   }
   return EVD_OK;

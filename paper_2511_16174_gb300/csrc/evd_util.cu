@@ -29,7 +29,7 @@ evd_status_t check_finite_lower(const PlanCore& pc, const double* A, int64_t lda
   for (int64_t j0 = 0; j0 < pc.n; j0 += 65535) {
     int64_t cols = pc.n - j0 < 65535 ? pc.n - j0 : 65535;
     dim3 grid(4, (unsigned)cols);
-    k_check_finite_lower<<<grid, 256, 0, pc.stream>>>(A + j0 * lda + j0, lda, pc.n - j0, pc.status);
+    k_check_finite_lower<<<grid, 256, 0, pc.stream>>>(A + j0 * lda + j0, lda, pc.n - j0, pc.status); count_launch();
   }
   EVD_CUDA_TRY(cudaGetLastError());
   return EVD_OK;
@@ -49,7 +49,7 @@ evd_status_t copy_lower_to_full(const double* A, int64_t lda, double* B, int64_t
                                 cudaStream_t s) {
   if (n == 0) return EVD_OK;
   dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(n, 32));
-  k_copy_lower_to_full<<<grid, dim3(32, 32), 0, s>>>(A, lda, B, ldb, n);
+  k_copy_lower_to_full<<<grid, dim3(32, 32), 0, s>>>(A, lda, B, ldb, n); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   return EVD_OK;
 }
@@ -71,7 +71,7 @@ __global__ void k_set_identity(double* Q, int64_t ldq, int64_t n, int64_t j0) {
 evd_status_t set_identity(double* Q, int64_t ldq, int64_t n, cudaStream_t s) {
   for (int64_t j0 = 0; j0 < n; j0 += 65535) {
     int64_t cols = n - j0 < 65535 ? n - j0 : 65535;
-    k_set_identity<<<dim3(4, (unsigned)cols), 256, 0, s>>>(Q, ldq, n, j0);
+    k_set_identity<<<dim3(4, (unsigned)cols), 256, 0, s>>>(Q, ldq, n, j0); count_launch();
   }
   EVD_CUDA_TRY(cudaGetLastError());
   return EVD_OK;

@@ -51,6 +51,12 @@ _SIGS = {
     "evd_dgemm": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64,
                    _int, _vp, _sz, _vp], _int),
     "evd_autotune": ([_i64, _int, _int, ctypes.c_char_p, ctypes.POINTER(_int), ctypes.POINTER(_int)], _int),
+    "evd_stats_enable": ([_int], None),
+    "evd_stats_reset": ([], None),
+    "evd_launch_count": ([], _i64),
+    "evd_stats_categories": ([ctypes.c_char_p, _int], _int),
+    "evd_stats_query": ([ctypes.c_char_p, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),
+                         ctypes.POINTER(_i64)], _int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -232,3 +238,29 @@ def autotune(n, job="V", prec="fp64", cache_path=None):
     _check(_lib.evd_autotune(int(n), jb, pr, cache_path.encode() if cache_path else None, ctypes.byref(b),
                              ctypes.byref(nb)), "evd_autotune")
     return b.value, nb.value
+
+
+# ---------------------------------------------------------------- instrumentation
+def stats_enable(on=True):
+    _lib.evd_stats_enable(1 if on else 0)
+
+
+def stats_reset():
+    _lib.evd_stats_reset()
+
+
+def launch_count():
+    return int(_lib.evd_launch_count())
+
+
+def stats():
+    """{category: (ms, flops, bytes, calls)} of everything recorded since the reset."""
+    buf = ctypes.create_string_buffer(8192)
+    _lib.evd_stats_categories(buf, 8192)
+    out = {}
+    for name in [c for c in buf.value.decode().split("\n") if c]:
+        ms, fl, by, ca = _dbl(), _dbl(), _dbl(), _i64()
+        _check(_lib.evd_stats_query(name.encode(), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by),
+                                    ctypes.byref(ca)), "evd_stats_query")
+        out[name] = (ms.value, fl.value, by.value, ca.value)
+    return out

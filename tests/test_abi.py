@@ -12,7 +12,7 @@ ROOT = Path(__file__).resolve().parents[1]
 def declared_functions():
     text = (ROOT / "include" / "evd.h").read_text()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:evd_status_t|void|const char\*)\s+(evd_\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:evd_status_t|void|const char\*|int64_t|int)\s+(evd_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

@@ -412,6 +412,7 @@ evd_status_t evd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k
   Gemm g;
   g.ta = transa; g.tb = transb; g.m = m; g.n = n; g.k = k; g.alpha = alpha; g.A = A; g.lda = lda;
   g.B = B; g.ldb = ldb; g.beta = beta; g.C = C; g.ldc = ldc;
+  g.force_tc = true;
   return gemm(g, slices, ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 

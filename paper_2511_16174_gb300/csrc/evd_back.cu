@@ -120,18 +120,21 @@ evd_status_t sbr_back_run(const PlanCore& pc, const double* A, const double* sbr
     EVD_CUDA_TRY(cudaGetLastError());
     // Wp = V^T X(r0:, :)   (kb x n)
     Gemm g1;
+    g1.status = pc.status;
     g1.ta = 'T'; g1.m = kb; g1.n = n; g1.k = m; g1.A = w.Vp; g1.lda = n; g1.B = Q + r0; g1.ldb = ldq;
     g1.C = w.Wp; g1.ldc = b; g1.alpha = 1.0; g1.beta = 0.0;
     evd_status_t st = gemm(g1, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
     // Tp = T Wp  (kb x n), T upper triangular kb x kb (ld b)
     Gemm g2;
+    g2.status = pc.status;
     g2.m = kb; g2.n = n; g2.k = kb; g2.A = sbr_T + (size_t)p * b * b; g2.lda = b; g2.B = w.Wp; g2.ldb = b;
     g2.C = w.Tp; g2.ldc = b; g2.alpha = 1.0; g2.beta = 0.0;
     st = gemm(g2, 0, nullptr, 0, s);
     if (st != EVD_OK) return st;
     // X(r0:, :) -= V Tp
     Gemm g3;
+    g3.status = pc.status;
     g3.m = m; g3.n = n; g3.k = kb; g3.A = w.Vp; g3.lda = n; g3.B = w.Tp; g3.ldb = b;
     g3.C = Q + r0; g3.ldc = ldq; g3.alpha = -1.0; g3.beta = 1.0;
     st = gemm(g3, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);

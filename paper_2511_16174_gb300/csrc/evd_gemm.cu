@@ -109,7 +109,7 @@ evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes
     EVD_CUDA_TRY(cudaGetLastError());
     return EVD_OK;
   }
-  if (slices > 0 && ozaki_eligible(g)) return ozaki_gemm(g, slices, scratch, scratch_bytes, s);
+  if (slices > 0 && (g.force_tc || ozaki_eligible(g))) return ozaki_gemm(g, slices, scratch, scratch_bytes, s);
   dim3 grid((unsigned)ceil_div(g.m, BM), (unsigned)ceil_div(g.n, BN));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
   const double flops = (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;

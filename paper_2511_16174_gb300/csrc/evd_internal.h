@@ -64,6 +64,11 @@ struct Gemm {
   bool lower = false;
   // A is symmetric with only its lower triangle stored (op(A) = A, m == k).
   bool a_sym_lower = false;
+  // device status word that bounded waits report timeouts to (nullptr: the
+  // library's own word for stand-alone products)
+  int* status = nullptr;
+  // use the tensor-core product whenever slices > 0 (stand-alone requests)
+  bool force_tc = false;
 };
 
 // Scratch a product needs (bytes) and the call itself.

@@ -1,19 +1,539 @@
-// Tensor-core split product (placeholder until the tcgen05 kernels land).
+// FP64-accurate dense products on the tcgen05 tensor cores (sm_103a).
+//
+// The FP64 operands are split into s bfloat16 slices (Ozaki-style error-free
+// splitting with balanced base-2^7 digits, after a power-of-two scaling of every row
+// of the left operand and every column of the right operand):
+//     a_rk = 2^(e_r) sum_t sigma_t 2^(-7 (t+1)),  |sigma_0| <= 128, |sigma_t| <= 64.
+// A digit is an integer of at most 8 significant bits, so it is exact in bfloat16;
+// a product of two digits is exact in FP32.  The kernel forms, for every weight
+// k = t + u <= s-1, S_k = sum over pairs (t, u) and over K of sigma^A_t sigma^B_u with
+// tcgen05.mma kind::f16 into an FP32 accumulator in tensor memory.  An accumulator
+// drained every 256 K-elements never exceeds (k+3) 2^12 * 256 <= 2^24 in magnitude,
+// so every partial sum is an exact integer; drains are converted to int64 and
+// combined exactly, with left shifts only, into two accumulators
+//     R_hi = sum_{k <= H} S_k 2^(7 (H - k))      H = min(s-1, 3)
+//     R_lo = sum_{4 <= k <= s-1} S_k 2^(7 (s-1-k))
+// (both stay below 2^53 for K <= 2^17), and finally
+// C = alpha (2^(e_r + f_c - 14 - 7H) R_hi + 2^(e_r + f_c - 14 - 7(s-1)) R_lo) + beta C
+// in FP64.
+//
+// Kernel structure (one CTA per 128 x 64 tile of C, 320 threads):
+//   warp 0      TMA producer: one 3-D box per operand and stage carries all s
+//               slices (16 K-elements, 32-byte rows, 32-byte swizzle), 4 stages.
+//   warp 1      tensor-memory allocation (512 columns) and the single MMA-issuing
+//               thread: per stage, every slice pair (t, u) with t + u <= s-1.
+//   warps 2..9  epilogue: one accumulator per weight (64 columns each), drained on a
+//               staggered schedule (one weight every other stage) into int64
+//               registers, then the FP64 write of C.
+// Every mbarrier wait is bounded; on timeout the CTA raises the abort flag, sets
+// EVD_ERR_TIMEOUT in the status word and leaves after freeing tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "device_util.cuh"
 #include "evd_ozaki.h"
 
 namespace evd {
 
-size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
-  (void)m; (void)n; (void)k; (void)slices;
-  return 256;
+namespace {
+
+constexpr int OZ_BM = 128;        // tile rows (tensor-memory lanes)
+constexpr int OZ_BN = 64;         // tile columns (per weight accumulator)
+constexpr int OZ_KS = 16;         // K-elements per stage (one MMA K-step, 32-byte rows)
+constexpr int OZ_MAXS = 8;        // slices
+constexpr int OZ_STAGES = 4;
+constexpr int OZ_THREADS = 320;
+constexpr int OZ_PERIOD = 16;     // stages between two drains of one weight (256 K-elements)
+constexpr long long OZ_WAIT_LIMIT = 1ll << 26;
+
+// ------------------------------------------------------------------ operand views
+// Element (rho, kappa) of an operand seen as rows x K:
+//   mode 0: p[rho + kappa ld]   mode 1: p[kappa + rho ld]
+//   mode 2: symmetric, lower triangle stored: p[max + min ld]
+struct View {
+  const double* p;
+  int64_t ld;
+  int mode;
+  int64_t rows, K;
+  __device__ __forceinline__ double get(int64_t r, int64_t k) const {
+    if (mode == 0) return p[r + k * ld];
+    if (mode == 1) return p[k + r * ld];
+    return (r >= k) ? p[r + k * ld] : p[k + r * ld];
+  }
+  __device__ __forceinline__ bool row_contig() const { return mode != 1; }
+};
+
+__device__ __forceinline__ void load_tile32(const View& v, int64_t r0, int64_t k0, double (*t)[33]) {
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int idx = tid; idx < 1024; idx += 256) {
+    const int a = idx & 31, b = idx >> 5;
+    const int r = v.row_contig() ? a : b, k = v.row_contig() ? b : a;
+    const int64_t R = r0 + r, KK = k0 + k;
+    t[r][k] = (R < v.rows && KK < v.K) ? v.get(R, KK) : 0.0;
+  }
 }
-bool ozaki_eligible(const Gemm& g) {
-  (void)g;
+
+// Max biased exponent of each row, atomicMax into ex[] (pre-zeroed).
+__global__ void k_row_exponent(const View v, int* ex, int64_t kspan) {
+  __shared__ double t[32][33];
+  __shared__ int red[8][32];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int64_t kb = (int64_t)blockIdx.y * kspan;
+  int mx = 0;
+  for (int64_t k0 = kb; k0 < kb + kspan && k0 < v.K; k0 += 32) {
+    __syncthreads();
+    load_tile32(v, r0, k0, t);
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(t[threadIdx.x][k]);
+      mx = max(mx, (int)((bits >> 52) & 0x7FF));
+    }
+  }
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    for (int y = 1; y < 8; ++y) mx = max(mx, red[y][threadIdx.x]);
+    if (r0 + threadIdx.x < v.rows && mx > 0) atomicMax(ex + r0 + threadIdx.x, mx);
+  }
+}
+
+// Balanced base-128 digits of T = round_half_away(x 2^(7s - e)).
+__device__ __forceinline__ void ozaki_digits(double x, int e, int s, int* dg) {
+  const long long bits = __double_as_longlong(x);
+  int E = (int)((bits >> 52) & 0x7FF);
+  long long m = bits & 0xFFFFFFFFFFFFFll;
+  long long T = 0;
+  if (E != 0 || m != 0) {
+    if (E == 0) E = 1; else m |= (1ll << 52);
+    const int sh = E - 1075 + 7 * s - e;  // |x| = m 2^(E - 1075);  T = m 2^sh
+    if (sh >= 0) T = m << sh;
+    else {
+      const int r = -sh;
+      T = (r >= 63) ? 0 : ((m + (1ll << (r - 1))) >> r);
+    }
+    if (bits < 0) T = -T;
+  }
+  for (int t = s - 1; t >= 1; --t) {
+    const long long r = ((T + 64) & 127) - 64;
+    dg[t] = (int)r;
+    T = (T - r) >> 7;
+  }
+  dg[0] = (int)T;
+}
+
+// Slices S[t][rho][kappa] (bfloat16, K-major, rows_pad x K_pad per slice) and the
+// frexp exponent per row (ex holds the max biased exponent on entry).
+__global__ void k_split(const View v, const int* ex_biased, int* ex_frexp, int s, int64_t rows_pad, int64_t K_pad,
+                        __nv_bfloat16* S) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  load_tile32(v, r0, k0, t);
+  __syncthreads();
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  // each thread: row r = tid / 16 + 16 j, kappa pair (2 q, 2 q + 1) with q = tid % 16
+  const int q = tid & 15;
+  for (int rr = tid >> 4; rr < 32; rr += 16) {
+    const int64_t R = r0 + rr;
+    int eb = (R < v.rows) ? ex_biased[R] : 0;
+    const int e = (eb > 0) ? eb - 1022 : -1022;
+    if (k0 == 0 && q == 0 && R < rows_pad) ex_frexp[R] = e;
+    int d0[OZ_MAXS], d1[OZ_MAXS];
+    ozaki_digits(t[rr][2 * q], e, s, d0);
+    ozaki_digits(t[rr][2 * q + 1], e, s, d1);
+    for (int tt = 0; tt < s; ++tt) {
+      __nv_bfloat162 h;
+      h.x = __float2bfloat16_rn((float)d0[tt]);
+      h.y = __float2bfloat16_rn((float)d1[tt]);
+      *reinterpret_cast<__nv_bfloat162*>(S + ((size_t)tt * rows_pad + R) * K_pad + k0 + 2 * q) = h;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; raises *abort (shared) and the status word on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort, int* st, int where) {
+  for (long long i = 0; i < OZ_WAIT_LIMIT; ++i) {
+    if (mbar_try(a, parity)) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  dev_set_status(st, EVD_ERR_TIMEOUT, where);
   return false;
 }
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+// K-major operand tile, 32-byte rows, 32-byte swizzle: SBO = 8 rows x 32 B.
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;    // stride byte offset: 8 rows x 32 B
+  d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
+  d |= (uint64_t)6 << 61;             // 32-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct MmaArgs {
+  int64_t m, n;
+  int s;            // slices
+  int nst;          // stages = K_pad / OZ_KS
+  uint32_t tmem_cols;
+  const int* ea;    // frexp exponents of the rows of the left operand
+  const int* eb;    // ... of the columns of the right operand
+  double* C;
+  int64_t ldc;
+  double alpha, beta;
+  int lower;
+  int* st;
+};
+
+__device__ __forceinline__ bool drain_after(int j, int k, int nst) {
+  return ((j + 2 * k) % OZ_PERIOD == OZ_PERIOD - 1) || (j == nst - 1);
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_ozaki_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const MmaArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  const int64_t m0 = (int64_t)blockIdx.x * OZ_BM, n0 = (int64_t)blockIdx.y * OZ_BN;
+  if (a.lower && n0 > m0 + OZ_BM - 1) return;  // tile strictly above the diagonal
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int s = a.s, L = s - 1;
+  const uint32_t a_bytes = (uint32_t)s * OZ_BM * OZ_KS * 2, b_bytes = (uint32_t)s * OZ_BN * OZ_KS * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + OZ_STAGES;
+  uint64_t* accf = bars + 2 * OZ_STAGES;
+  uint64_t* acce = bars + 2 * OZ_STAGES + OZ_MAXS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 2 * OZ_MAXS);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < OZ_STAGES; ++i) { mbar_init(smem_u32(full + i), 1); mbar_init(smem_u32(empty + i), 1); }
+    for (int k = 0; k < OZ_MAXS; ++k) { mbar_init(smem_u32(accf + k), 1); mbar_init(smem_u32(acce + k), 8); }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int issued = 0;
+      for (int j = 0; j < a.nst; ++j) {
+        const int si = j % OZ_STAGES, round = j / OZ_STAGES;
+        if (round > 0 && !mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9001)) break;
+        uint8_t* sa = smem + si * stage_bytes;
+        const uint32_t fb = smem_u32(full + si);
+        mbar_expect_tx(fb, stage_bytes);
+        tma_load_3d(smem_u32(sa), &tmA, j * OZ_KS, (int)m0, 0, fb);
+        tma_load_3d(smem_u32(sa + a_bytes), &tmB, j * OZ_KS, (int)n0, 0, fb);
+        ++issued;
+      }
+      if (*abort) {
+        // let the copies already in flight land before the CTA exits
+        for (int j = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); j < issued; ++j) {
+          const int si = j % OZ_STAGES, round = j / OZ_STAGES;
+          for (long long i = 0; i < OZ_WAIT_LIMIT && !mbar_try(smem_u32(full + si), round & 1); ++i) {}
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                             ((uint32_t)(OZ_BM >> 4) << 24);
+      int chunks[OZ_MAXS];
+      for (int k = 0; k < OZ_MAXS; ++k) chunks[k] = 0;
+      for (int j = 0; j < a.nst && !*abort; ++j) {
+        const int si = j % OZ_STAGES, round = j / OZ_STAGES;
+        if (!mbar_wait(smem_u32(full + si), round & 1, abort, a.st, 9002)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + si * stage_bytes);
+        const uint32_t sb = sa + a_bytes;
+        for (int k = 0; k <= L; ++k) {
+          const bool fresh = (j == 0) || drain_after(j - 1, k, a.nst);
+          if (fresh && chunks[k] > 0) {
+            if (!mbar_wait(smem_u32(acce + k), (chunks[k] - 1) & 1, abort, a.st, 9003)) break;
+            tc_fence_after();
+          }
+          const int tlo = (k - L > 0) ? k - L : 0, thi = (k < L) ? k : L;
+          for (int t = tlo; t <= thi; ++t) {
+            const int u = k - t;
+            const uint64_t da = desc_sw32(sa + (uint32_t)t * OZ_BM * OZ_KS * 2);
+            const uint64_t db = desc_sw32(sb + (uint32_t)u * OZ_BN * OZ_KS * 2);
+            tc_mma(tmem + (uint32_t)(k * OZ_BN), da, db, idesc, (fresh && t == tlo) ? 0u : 1u);
+          }
+          if (drain_after(j, k, a.nst)) {
+            tc_commit(smem_u32(accf + k));
+            ++chunks[k];
+          }
+        }
+        tc_commit(smem_u32(empty + si));
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 2..9
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int64_t row = m0 + quad * 32 + lane;
+    const int H = (L < 3) ? L : 3;
+    long long Rh[32], Rl[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) { Rh[c] = 0; Rl[c] = 0; }
+    int drains[OZ_MAXS];
+    for (int k = 0; k < OZ_MAXS; ++k) drains[k] = 0;
+    bool ok = true;
+    for (int j = 0; j < a.nst && ok; ++j) {
+      for (int k = 0; k <= L; ++k) {
+        if (!drain_after(j, k, a.nst)) continue;
+        if (!mbar_wait(smem_u32(accf + k), drains[k] & 1, abort, a.st, 9004)) { ok = false; break; }
+        ++drains[k];
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + half * 32);
+        const bool hi = (k <= 3);
+        const int sh = hi ? 7 * (H - k) : 7 * (L - k);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[16];
+          tc_ld16(taddr + 16 * h, v);
+          if (hi) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) Rh[16 * h + c] += (long long)__float2int_rn(v[c]) << sh;
+          } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) Rl[16 * h + c] += (long long)__float2int_rn(v[c]) << sh;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(acce + k));
+      }
+    }
+    if (ok && row < a.m) {
+      const int er = a.ea[row];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int64_t col = n0 + half * 32 + c;
+        if (col < a.n && !(a.lower && row < col)) {
+          const int ex = er + a.eb[col] - 14;
+          double v = ldexp((double)Rh[c], ex - 7 * H);
+          if (L >= 4) v += ldexp((double)Rl[c], ex - 7 * L);
+          v *= a.alpha;
+          double* p = a.C + row + col * a.ldc;
+          if (a.beta != 0.0) v = fma(a.beta, *p, v);
+          *p = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D map over S[s][rows_pad][K_pad] (bf16), box {16, box_rows, s}, 32-byte swizzle.
+bool make_map(CUtensorMap* tm, void* base, int64_t K_pad, int64_t rows_pad, int s, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K_pad, (cuuint64_t)rows_pad, (cuuint64_t)s};
+  cuuint64_t strides[2] = {(cuuint64_t)K_pad * 2, (cuuint64_t)rows_pad * K_pad * 2};
+  cuuint32_t box[3] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, (cuuint32_t)s};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+struct Pads {
+  int64_t m_pad, n_pad, k_pad;
+};
+Pads pads(int64_t m, int64_t n, int64_t k) {
+  return {ceil_div(m, OZ_BM) * OZ_BM, ceil_div(n, OZ_BN) * OZ_BN, ceil_div(k, 32) * 32};
+}
+
+size_t smem_bytes(int s) {
+  return 1024 + (size_t)OZ_STAGES * s * (OZ_BM + OZ_BN) * OZ_KS * 2 + (2 * OZ_STAGES + 2 * OZ_MAXS) * 8 + 16;
+}
+
+}  // namespace
+
+size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
+  if (slices <= 0) return 0;
+  Pads p = pads(m, n, k);
+  Carver c(nullptr);
+  c.take<__nv_bfloat16>((size_t)slices * p.m_pad * p.k_pad);
+  c.take<__nv_bfloat16>((size_t)slices * p.n_pad * p.k_pad);
+  c.take<int>((size_t)p.m_pad);
+  c.take<int>((size_t)p.n_pad);
+  c.take<int>((size_t)p.m_pad);
+  c.take<int>((size_t)p.n_pad);
+  return c.off + 256;
+}
+
+bool ozaki_eligible(const Gemm& g) {
+  if (g.k < 32 || g.m < 16 || g.n < 16) return false;
+  if (g.m > (int64_t)1 << 30 || g.n > (int64_t)1 << 30 || g.k > ((int64_t)1 << 17)) return false;
+  return 2.0 * (double)g.m * (double)g.n * (double)g.k >= 6.7e7;
+}
+
 evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes, cudaStream_t s) {
-  (void)g; (void)slices; (void)scratch; (void)scratch_bytes; (void)s;
-  return EVD_ERR_NOT_SUPPORTED;
+  if (slices < 1 || slices > OZ_MAXS) return EVD_ERR_INVALID_ARG;
+  if (scratch_bytes < ozaki_scratch_bytes(g.m, g.n, g.k, slices) || !scratch) return EVD_ERR_WORKSPACE;
+  if (g.k > ((int64_t)1 << 17)) return EVD_ERR_NOT_SUPPORTED;  // exactness bound of the int64 sums
+  const Pads p = pads(g.m, g.n, g.k);
+  Carver c(scratch);
+  __nv_bfloat16* SA = c.take<__nv_bfloat16>((size_t)slices * p.m_pad * p.k_pad);
+  __nv_bfloat16* SB = c.take<__nv_bfloat16>((size_t)slices * p.n_pad * p.k_pad);
+  int* exA = c.take<int>((size_t)p.m_pad);
+  int* exB = c.take<int>((size_t)p.n_pad);
+  int* eA = c.take<int>((size_t)p.m_pad);
+  int* eB = c.take<int>((size_t)p.n_pad);
+  View va, vb;
+  va.p = g.A; va.ld = g.lda; va.rows = g.m; va.K = g.k;
+  va.mode = g.a_sym_lower ? 2 : (g.ta == 'N' ? 0 : 1);
+  vb.p = g.B; vb.ld = g.ldb; vb.rows = g.n; vb.K = g.k;
+  vb.mode = (g.tb == 'N') ? 1 : 0;
+  const double flops = (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;
+  {
+    StatScope sc("gemm_tc_split_prep", s, 0.0,
+                 8.0 * (double)(g.m + g.n) * (double)g.k * 2.0 + 2.0 * slices * (double)(p.m_pad + p.n_pad) * p.k_pad);
+    EVD_CUDA_TRY(cudaMemsetAsync(exA, 0, sizeof(int) * p.m_pad, s));
+    EVD_CUDA_TRY(cudaMemsetAsync(exB, 0, sizeof(int) * p.n_pad, s));
+    const int64_t kspan = 1024;
+    dim3 blk(32, 8);
+    k_row_exponent<<<dim3((unsigned)ceil_div(g.m, 32), (unsigned)ceil_div(g.k, kspan)), blk, 0, s>>>(va, exA, kspan); count_launch();
+    k_row_exponent<<<dim3((unsigned)ceil_div(g.n, 32), (unsigned)ceil_div(g.k, kspan)), blk, 0, s>>>(vb, exB, kspan); count_launch();
+    k_split<<<dim3((unsigned)(p.m_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(va, exA, eA, slices, p.m_pad,
+                                                                                   p.k_pad, SA); count_launch();
+    k_split<<<dim3((unsigned)(p.n_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(vb, exB, eB, slices, p.n_pad,
+                                                                                   p.k_pad, SB); count_launch();
+    EVD_CUDA_TRY(cudaGetLastError());
+  }
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, SA, p.k_pad, p.m_pad, slices, OZ_BM) || !make_map(&tmB, SB, p.k_pad, p.n_pad, slices, OZ_BN))
+    return EVD_ERR_CUDA;
+  MmaArgs a;
+  a.m = g.m; a.n = g.n; a.s = slices; a.nst = (int)(p.k_pad / OZ_KS);
+  uint32_t cols = 64;
+  while (cols < (uint32_t)(slices * OZ_BN)) cols <<= 1;
+  a.tmem_cols = cols;
+  a.ea = eA; a.eb = eB; a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha; a.beta = g.beta;
+  a.lower = g.lower ? 1 : 0; a.st = nullptr;
+  static int* d_dummy_status = nullptr;  // status word for timeouts of standalone products
+  if (!d_dummy_status) {
+    if (cudaMalloc(&d_dummy_status, sizeof(int) * kStatusWords) != cudaSuccess) return EVD_ERR_OOM;
+    cudaMemset(d_dummy_status, 0, sizeof(int) * kStatusWords);
+  }
+  a.st = g.status ? g.status : d_dummy_status;
+  const size_t smem = smem_bytes(slices);
+  static bool attr_set = false;
+  if (!attr_set) {
+    EVD_CUDA_TRY(cudaFuncSetAttribute(k_ozaki_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_bytes(OZ_MAXS)));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN));
+  if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
+  StatScope sc("gemm_tc_split", s, flops * (double)(slices * (slices + 1) / 2));
+  k_ozaki_mma<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, a); count_launch();
+  EVD_CUDA_TRY(cudaGetLastError());
+  return EVD_OK;
 }
 
 }  // namespace evd

@@ -112,6 +112,7 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
   for (int it = 0; it < iters; ++it) {
     // R = I - X^T X
     Gemm g1;
+    g1.status = pc.status;
     g1.ta = 'T'; g1.m = n; g1.n = n; g1.k = n; g1.A = Q; g1.lda = ldq; g1.B = Q; g1.ldb = ldq;
     g1.C = rw.R; g1.ldc = n; g1.alpha = -1.0; g1.beta = 0.0;
     evd_status_t st = gemm(g1, pc.ref_slices, rw.gemm_ws, rw.gemm_ws_bytes, s);
@@ -119,12 +120,14 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
     k_add_identity<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(rw.R, n, n); count_launch();
     // AX = A0 X (A0 symmetric, lower stored)
     Gemm g2;
+    g2.status = pc.status;
     g2.m = n; g2.n = n; g2.k = n; g2.A = A0; g2.lda = lda0; g2.a_sym_lower = true; g2.B = Q; g2.ldb = ldq;
     g2.C = rw.AX; g2.ldc = n; g2.alpha = 1.0; g2.beta = 0.0;
     st = gemm(g2, pc.ref_slices, rw.gemm_ws, rw.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
     // S = X^T AX
     Gemm g3;
+    g3.status = pc.status;
     g3.ta = 'T'; g3.m = n; g3.n = n; g3.k = n; g3.A = Q; g3.lda = ldq; g3.B = rw.AX; g3.ldb = n;
     g3.C = rw.S; g3.ldc = n; g3.alpha = 1.0; g3.beta = 0.0;
     st = gemm(g3, pc.ref_slices, rw.gemm_ws, rw.gemm_ws_bytes, s);
@@ -138,6 +141,7 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
     EVD_CUDA_TRY(cudaGetLastError());
     // X <- X + X E   (product into AX, then add)
     Gemm g4;
+    g4.status = pc.status;
     g4.m = n; g4.n = n; g4.k = n; g4.A = Q; g4.lda = ldq; g4.B = rw.S; g4.ldb = n;
     g4.C = rw.AX; g4.ldc = n; g4.alpha = 1.0; g4.beta = 0.0;
     st = gemm(g4, pc.ref_slices, rw.gemm_ws, rw.gemm_ws_bytes, s);

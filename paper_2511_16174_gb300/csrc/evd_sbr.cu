@@ -228,11 +228,13 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
     // ---- Eq. 1: Y = A2 W ; M = W^T Y ; Z = Y - 1/2 V M ; A2 -= V Z^T + Z V^T
     double* A2 = A + r0 + r0 * lda;
     Gemm g1;
+    g1.status = pc.status;
     g1.m = m; g1.n = kb; g1.k = m; g1.A = A2; g1.lda = lda; g1.a_sym_lower = true;
     g1.B = w.W; g1.ldb = n; g1.C = w.Y; g1.ldc = n; g1.alpha = 1.0; g1.beta = 0.0;
     evd_status_t st = gemm(g1, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
     Gemm g2;
+    g2.status = pc.status;
     g2.ta = 'T'; g2.m = kb; g2.n = kb; g2.k = m; g2.A = w.W; g2.lda = n; g2.B = w.Y; g2.ldb = n;
     g2.C = w.M; g2.ldc = b; g2.alpha = 1.0; g2.beta = 0.0;
     st = gemm(g2, 0, nullptr, 0, s);
@@ -240,11 +242,13 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
     EVD_CUDA_TRY(cudaMemcpy2DAsync(w.Z, n * sizeof(double), w.Y, n * sizeof(double), m * sizeof(double), kb,
                                    cudaMemcpyDeviceToDevice, s));
     Gemm g3;
+    g3.status = pc.status;
     g3.m = m; g3.n = kb; g3.k = kb; g3.A = w.V; g3.lda = n; g3.B = w.M; g3.ldb = b; g3.C = w.Z; g3.ldc = n;
     g3.alpha = -0.5; g3.beta = 1.0;
     st = gemm(g3, 0, nullptr, 0, s);
     if (st != EVD_OK) return st;
     Gemm g4;
+    g4.status = pc.status;
     g4.tb = 'T'; g4.m = m; g4.n = m; g4.k = kb; g4.A = w.V; g4.lda = n; g4.B = w.Z; g4.ldb = n;
     g4.C = A2; g4.ldc = lda; g4.alpha = -1.0; g4.beta = 1.0; g4.lower = true;
     st = gemm(g4, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);

@@ -31,10 +31,13 @@ __device__ inline void st_release(int* p, int v) {
 // EVD_ERR_TIMEOUT (info = where) and the function returns false.  Also returns
 // false as soon as another CTA has raised the abort flag (status[2]).
 __device__ inline bool wait_geq(const int* flag, int target, int* st, int where) {
+  // busy polling first (the waits on the critical path are short), then back off
+  for (int it = 0; it < 20000; ++it)
+    if (ld_acquire(flag) >= target) return true;
   for (long long it = 0; it < kSpinLimit; ++it) {
     if (ld_acquire(flag) >= target) return true;
     if (ld_acquire(st + 2) != 0) return false;
-    __nanosleep(256);
+    __nanosleep(64);
   }
   dev_set_status(st, EVD_ERR_TIMEOUT, where);
   atomicExch(st + 2, 1);
@@ -58,10 +61,12 @@ __device__ inline bool grid_barrier(unsigned* bar, unsigned nblocks, int* st, in
       atomicAdd(bar + 1, 1u);
     } else {
       long long it = 0;
-      for (; it < kSpinLimit; ++it) {
+      bool done = false;
+      for (int q = 0; q < 20000 && !done; ++q) done = (ld_acquire_u(bar + 1) != gen);
+      for (; !done && it < kSpinLimit; ++it) {
         if (ld_acquire_u(bar + 1) != gen) break;
         if (ld_acquire(st + 2) != 0) { ok_s = 0; break; }
-        __nanosleep(64);
+        __nanosleep(32);
       }
       if (it == kSpinLimit) {
         dev_set_status(st, EVD_ERR_TIMEOUT, where);

@@ -76,6 +76,10 @@ size_t back_union_bytes(int64_t n, int b) {
   c.take<double>((size_t)n * b);
   c.take<double>((size_t)n * b);
   c.take<double>((size_t)n * b);
+  const int64_t kmax = n / b + 2, h = 2 * b - 1;
+  c.take<double>((size_t)kmax * h * b);
+  c.take<double>((size_t)kmax * h * b);
+  c.take<double>((size_t)n * b);
   return c.off;
 }
 size_t refine_union_bytes(int64_t n) {
@@ -170,6 +174,10 @@ BackWork back_work(const evd_plan_s* p, const WsLayout& L) {
   w.Vp = c.take<double>((size_t)n * b);
   w.Wp = c.take<double>((size_t)n * b);
   w.Tp = c.take<double>((size_t)n * b);
+  const int64_t kmax = n / b + 2, h = 2 * b - 1;
+  w.Vg = c.take<double>((size_t)kmax * h * b);
+  w.Yg = c.take<double>((size_t)kmax * h * b);
+  w.Wt = c.take<double>((size_t)n * b);
   w.gemm_ws = L.gemm_ws;
   w.gemm_ws_bytes = L.gemm_bytes;
   return w;
@@ -242,6 +250,7 @@ evd_status_t evd_plan_create(evd_plan_t* plan, int64_t n, int64_t lda, evd_job_t
   c.refine_iters = (prec == EVD_SPLIT_BF16) ? 2 : 0;
   c.stream = static_cast<cudaStream_t>(stream);
   if (const char* s = getenv("EVD_SLICES")) c.slices = atoi(s);
+  if (const char* s = getenv("EVD_PANEL_CTAS")) c.panel_ctas = std::max(1, atoi(s));
   cudaGetDevice(&c.device);
   cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device);
   if (cudaMalloc(&p->d_status, sizeof(int) * kStatusWords) != cudaSuccess ||

@@ -79,6 +79,69 @@ __global__ void __launch_bounds__(BB_NT) k_bc_back(const double* __restrict__ U,
   }
 }
 
+// Compact WY factors of the BC reflector groups of one sweep block J: group k
+// holds the reflectors (j, k), j in [J g, J g + g), whose rows lie in
+// [R0, R0 + g + b - 1) with R0 = J g + 1 + k b; reflector j sits in column
+// i = j - J g at rows i .. i + b - 1 of the group.  For each group the kernel forms
+// V (h x g, explicit, zero outside the parallelogram), T (g x g upper triangular,
+// H_{j0} ... H_{j0+g-1} = I - V T V^T) and Y = V T.  One CTA per group.
+__global__ void __launch_bounds__(256) k_bcback_prep(const double* __restrict__ U, const double* __restrict__ Utau,
+                                                     int64_t n, int b, int g, int64_t J, int64_t kcount, double* Vg,
+                                                     double* Yg, int h) {
+  extern __shared__ double sp[];
+  double* V = sp;                 // V[r + i h], h x g
+  double* T = V + (size_t)h * g;  // T[p + i g]
+  double* tau = T + (size_t)g * g;
+  const int64_t k = blockIdx.x;
+  if (k >= kcount) return;
+  const int64_t nsweeps = n - 2;
+  for (int idx = threadIdx.x; idx < h * g; idx += blockDim.x) V[idx] = 0.0;
+  __syncthreads();
+  for (int i = threadIdx.y; i < g; i += blockDim.y) {  // (blockDim = 32 x 8)
+    const int64_t j = J * g + i;
+    double t = 0.0;
+    if (j < nsweeps && k < sweep_steps_b(n, b, j)) {
+      const int64_t idx = sweep_offset_b(n, b, j) + k;
+      t = Utau[idx];
+      const int64_t r0 = j + 1 + k * b;
+      const int m = (int)((r0 + b - 1 < n - 1) ? b : n - r0);
+      for (int q = threadIdx.x; q < m; q += 32) V[(i + q) + (size_t)i * h] = U[idx * b + q];
+    }
+    if (threadIdx.x == 0) tau[i] = t;
+  }
+  __syncthreads();
+  // T, column by column: T(0:i, i) = -tau_i T(0:i, 0:i) (V(:, 0:i)^T v_i)
+  double* gv = T + (size_t)g * g + g;  // g scratch
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int i = 0; i < g; ++i) {
+    const double ti = tau[i];
+    for (int l = tid; l < i; l += 256) {
+      double s = 0.0;
+      const int lo = i, hi = (l + b - 1 < h - 1) ? l + b - 1 : h - 1;
+      for (int r = lo; r <= hi; ++r) s += V[r + (size_t)l * h] * V[r + (size_t)i * h];
+      gv[l] = s;
+    }
+    __syncthreads();
+    for (int p = tid; p < g; p += 256) {
+      double s = 0.0;
+      if (p < i)
+        for (int l = p; l < i; ++l) s += T[p + (size_t)l * g] * gv[l];
+      T[p + (size_t)i * g] = (p < i) ? -ti * s : (p == i ? ti : 0.0);
+    }
+    __syncthreads();
+  }
+  // write V and Y = V T (h x g each, group k at offset k h g)
+  double* Vo = Vg + (size_t)k * h * g;
+  double* Yo = Yg + (size_t)k * h * g;
+  for (int idx = tid; idx < h * g; idx += 256) {
+    const int r = idx % h, i = idx / h;
+    double s = 0.0;
+    for (int l = 0; l <= i; ++l) s += V[r + (size_t)l * h] * T[l + (size_t)i * g];
+    Yo[idx] = s;
+    Vo[idx] = V[idx];
+  }
+}
+
 // Explicit V of SBR panel p: V(r, i) = 0 (r < i), 1 (r == i), A(r0 + r, c0 + i) (r > i).
 __global__ void k_explicit_v(const double* A, int64_t lda, int64_t r0, int64_t c0, int64_t m, int kb, double* V,
                              int64_t ldv) {
@@ -92,13 +155,57 @@ __global__ void k_explicit_v(const double* A, int64_t lda, int64_t r0, int64_t c
 }  // namespace
 
 evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w) {
-  (void)w;
   const int64_t n = pc.n;
   if (n < 3 || pc.b < 2) return EVD_OK;
-  const unsigned grid = (unsigned)ceil_div(n, BB_NC);
-  StatScope sc("bc_back", pc.stream, 4.0 * pc.b * (double)n * (double)bc_num_reflectors(n, pc.b));
-  k_bc_back<<<grid, BB_NT, 0, pc.stream>>>(bw.U, bw.Utau, n, pc.b, pc.b, Q, ldq); count_launch();
-  EVD_CUDA_TRY(cudaGetLastError());
+  const int b = pc.b, g = pc.b;
+  const int h = g + b - 1;
+  // small problems: reflector-by-reflector kernel on FP64 cores
+  if (pc.slices <= 0 || n < 1024 || !w.Vg) {
+    const unsigned grid = (unsigned)ceil_div(n, BB_NC);
+    StatScope sc("bc_back", pc.stream, 4.0 * pc.b * (double)n * (double)bc_num_reflectors(n, pc.b));
+    k_bc_back<<<grid, BB_NT, 0, pc.stream>>>(bw.U, bw.Utau, n, pc.b, pc.b, Q, ldq); count_launch();
+    EVD_CUDA_TRY(cudaGetLastError());
+    return EVD_OK;
+  }
+  cudaStream_t s = pc.stream;
+  const int64_t nsweeps = n - 2;
+  const int64_t nJ = ceil_div(nsweeps, g);
+  const size_t smem = ((size_t)h * g + (size_t)g * g + 2 * g) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    EVD_CUDA_TRY(cudaFuncSetAttribute(k_bcback_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  for (int64_t J = nJ - 1; J >= 0; --J) {
+    const int64_t kcount = sweep_steps_b(n, b, J * g);  // the block's first sweep has the most steps
+    if (kcount <= 0) continue;
+    {
+      StatScope sc("bc_back_prep", s);
+      k_bcback_prep<<<(unsigned)kcount, dim3(32, 8), smem, s>>>(bw.U, bw.Utau, n, b, g, J, kcount, w.Vg, w.Yg, h); count_launch();
+      EVD_CUDA_TRY(cudaGetLastError());
+    }
+    for (int64_t k = 0; k < kcount; ++k) {
+      const int64_t R0 = J * g + 1 + k * b;
+      const int64_t hh = std::min<int64_t>(h, n - R0);
+      if (hh <= 0) break;
+      const double* V = w.Vg + (size_t)k * h * g;
+      const double* Y = w.Yg + (size_t)k * h * g;
+      // W^T = X(R0:R0+hh, :)^T V   (n x g)
+      Gemm g1;
+      g1.status = pc.status;
+      g1.ta = 'T'; g1.m = n; g1.n = g; g1.k = hh; g1.A = Q + R0; g1.lda = ldq; g1.B = V; g1.ldb = h;
+      g1.C = w.Wt; g1.ldc = n; g1.alpha = 1.0; g1.beta = 0.0;
+      evd_status_t st = gemm(g1, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
+      if (st != EVD_OK) return st;
+      // X(R0:R0+hh, :) -= Y W
+      Gemm g2;
+      g2.status = pc.status;
+      g2.tb = 'T'; g2.m = hh; g2.n = n; g2.k = g; g2.A = Y; g2.lda = h; g2.B = w.Wt; g2.ldb = n;
+      g2.C = Q + R0; g2.ldc = ldq; g2.alpha = -1.0; g2.beta = 1.0;
+      st = gemm(g2, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
+      if (st != EVD_OK) return st;
+    }
+  }
   return EVD_OK;
 }
 

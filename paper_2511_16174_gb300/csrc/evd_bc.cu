@@ -165,6 +165,167 @@ __global__ void __launch_bounds__(BC_NT) k_bulge_chase(const BcArgs a) {
   }
 }
 
+// Shared-memory-staged form of the same step (b <= BM): the three blocks a step
+// touches -- the bulge A(R_k, c : r0-1), the diagonal block A(R_k, R_k) and the
+// block below A(r1+1 : r1+b, R_k) -- are read from the band once with coalesced
+// loads, updated in shared memory, and written back once.  Identical arithmetic to
+// k_bulge_chase, in the same order per entry.
+template <int BM>
+__global__ void __launch_bounds__(BC_NT) k_bulge_chase_smem(const BcArgs a) {
+  extern __shared__ double smb[];
+  constexpr int LD = BM + 1;
+  double* Ls = smb;             // Ls[t * LD + cc] = A(r0 + t, c + cc)
+  double* Ds = Ls + BM * LD;    // Ds[q * LD + p]  = A(r0 + p, r0 + q)   (both triangles)
+  double* Bs = Ds + BM * LD;    // Bs[t * LD + rr] = A(r1 + 1 + rr, r0 + t)
+  __shared__ double v[BM], wv[BM];
+  __shared__ double par[4];
+  const int b = a.b, ldb = 2 * b + 1;
+  const int64_t n = a.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t j = blockIdx.x; j + 3 <= n; j += gridDim.x) {
+    const int64_t K = sweep_steps(n, b, j);
+    const int64_t Kprev = (j > 0) ? sweep_steps(n, b, j - 1) : 0;
+    const int64_t uoff = sweep_offset(n, b, j);
+    for (int64_t k = 0; k < K; ++k) {
+      if (j > 0) {
+        int64_t need = k + BC_LAG;
+        if (need > Kprev) need = Kprev;
+        if (tid == 0) par[3] = wait_geq(a.prog + (j - 1), (int)need, a.st, (int)(j + 1)) ? 0.0 : 1.0;
+        __syncthreads();
+        if (par[3] != 0.0) return;
+      }
+      const int64_t r0 = j + 1 + k * b;
+      const int64_t r1 = (r0 + b - 1 < n - 1) ? r0 + b - 1 : n - 1;
+      const int m = (int)(r1 - r0 + 1);
+      const int64_t c = (k == 0) ? j : r0 - b;
+      const int ncol = (int)(r0 - c);                                   // 1 for k = 0, b otherwise
+      const int mb = (int)(((r1 + b < n - 1) ? r1 + b : n - 1) - r1);   // rows of the block below
+      // ---- load (2-D thread mapping: row = tid % BM, column stride BC_NT / BM)
+      constexpr int CS = BC_NT / BM;
+      const int tr = tid % BM, tc = tid / BM;
+      if (tr < m) {
+        for (int cc = tc; cc < ncol; cc += CS) Ls[tr * LD + cc] = bget(a.band, ldb, r0 + tr, c + cc);
+        for (int q = tc; q <= tr; q += CS) Ds[q * LD + tr] = bget(a.band, ldb, r0 + tr, r0 + q);
+      }
+      if (tr < mb)
+        for (int t = tc; t < m; t += CS) Bs[t * LD + tr] = bget(a.band, ldb, r1 + 1 + tr, r0 + t);
+      __syncthreads();
+      if (tr < m)
+        for (int q = tc; q < m; q += CS)
+          if (tr < q) Ds[q * LD + tr] = Ds[tr * LD + q];
+      // ---- reflector from x = Ls(:, 0)
+      if (warp == 0) {
+        double ss = 0.0;
+        for (int t = 1 + lane; t < m; t += 32) { const double x = Ls[t * LD]; ss += x * x; }
+        ss = warp_sum(ss);
+        if (lane == 0) {
+          const double alpha = Ls[0];
+          double tau = 0.0, beta = alpha, scale = 0.0;
+          if (ss != 0.0) {
+            const double nrm = sqrt(alpha * alpha + ss);
+            beta = (alpha >= 0.0) ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+          }
+          par[0] = tau; par[1] = beta; par[2] = scale;
+        }
+      }
+      __syncthreads();
+      const double tau = par[0], beta = par[1], scale = par[2];
+      if (tid < BM) v[tid] = (tid == 0) ? 1.0 : (tid < m ? Ls[tid * LD] * scale : 0.0);
+      __syncthreads();
+      if (a.U) {
+        const int64_t idx = uoff + k;
+        if (tid < b) a.U[idx * b + tid] = v[tid];
+        if (tid == 0) a.Utau[idx] = tau;
+      }
+      if (tid < m) Ls[tid * LD] = (tid == 0) ? beta : 0.0;
+      if (tau != 0.0) {
+        // TPR threads per row / column, each over every TPR-th index with two
+        // accumulators, combined with lane shuffles (the TPR lanes sit in one warp)
+        constexpr int TPR = BC_NT / BM;
+        const int grp = tid / TPR, sub = tid % TPR;
+        // left application to the rest of the bulge: columns 1 .. ncol-1
+        {
+          const int cc = 1 + grp;
+          double d0 = 0.0, d1 = 0.0;
+          if (cc < ncol) {
+            int t = sub;
+            for (; t + TPR < m; t += 2 * TPR) { d0 += v[t] * Ls[t * LD + cc]; d1 += v[t + TPR] * Ls[(t + TPR) * LD + cc]; }
+            if (t < m) d0 += v[t] * Ls[t * LD + cc];
+          }
+          double dot = d0 + d1;
+#pragma unroll
+          for (int o = TPR / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          if (cc < ncol) {
+            dot *= tau;
+            for (int t = sub; t < m; t += TPR) Ls[t * LD + cc] -= dot * v[t];
+          }
+        }
+        // two-sided on the diagonal block: w = tau D v
+        {
+          const int p = grp;
+          double d0 = 0.0, d1 = 0.0;
+          if (p < m) {
+            int q = sub;
+            for (; q + TPR < m; q += 2 * TPR) { d0 += Ds[q * LD + p] * v[q]; d1 += Ds[(q + TPR) * LD + p] * v[q + TPR]; }
+            if (q < m) d0 += Ds[q * LD + p] * v[q];
+          }
+          double dot = d0 + d1;
+#pragma unroll
+          for (int o = TPR / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          if (p < m && sub == 0) wv[p] = tau * dot;
+        }
+        // right application to the block below
+        {
+          const int rr = grp;
+          double d0 = 0.0, d1 = 0.0;
+          if (rr < mb) {
+            int t = sub;
+            for (; t + TPR < m; t += 2 * TPR) { d0 += Bs[t * LD + rr] * v[t]; d1 += Bs[(t + TPR) * LD + rr] * v[t + TPR]; }
+            if (t < m) d0 += Bs[t * LD + rr] * v[t];
+          }
+          double dot = d0 + d1;
+#pragma unroll
+          for (int o = TPR / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          if (rr < mb) {
+            dot *= tau;
+            for (int t = sub; t < m; t += TPR) Bs[t * LD + rr] -= dot * v[t];
+          }
+        }
+        __syncthreads();
+        if (warp == 0) {
+          double pv = 0.0;
+          for (int t = lane; t < m; t += 32) pv += wv[t] * v[t];
+          pv = warp_sum(pv);
+          if (lane == 0) par[2] = 0.5 * tau * pv;
+        }
+        __syncthreads();
+        const double alpha = par[2];
+        if (tid < m) wv[tid] -= alpha * v[tid];
+        __syncthreads();
+        // rank-2 update of the lower triangle
+        if (tr < m)
+          for (int q = tc; q <= tr; q += CS) Ds[q * LD + tr] -= v[tr] * wv[q] + wv[tr] * v[q];
+      }
+      __syncthreads();
+      // ---- write back
+      if (tr < m) {
+        for (int cc = tc; cc < ncol; cc += CS) bput(a.band, ldb, r0 + tr, c + cc, Ls[tr * LD + cc]);
+        for (int q = tc; q <= tr; q += CS) bput(a.band, ldb, r0 + tr, r0 + q, Ds[q * LD + tr]);
+      }
+      if (tr < mb)
+        for (int t = tc; t < m; t += CS) bput(a.band, ldb, r1 + 1 + tr, r0 + t, Bs[t * LD + tr]);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(a.prog + j, (int)(k + 1));
+      }
+    }
+    if (K == 0 && tid == 0) st_release(a.prog + j, 0);
+  }
+}
+
 __global__ void k_extract_tridiag(const double* band, int b, int64_t n, double* d, double* e) {
   const int ldb = 2 * b + 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -190,14 +351,24 @@ evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, b
     a.U = vectors ? w.U : nullptr;
     a.Utau = w.Utau;
     a.prog = w.prog; a.st = pc.status;
-    int maxG = max_coresident_blocks((const void*)k_bulge_chase, BC_NT, 0);
+    const void* kern = (const void*)k_bulge_chase;
+    size_t smem = 0;
+    if (pc.b <= 32) {
+      kern = (const void*)k_bulge_chase_smem<32>;
+      smem = 3 * 32 * 33 * sizeof(double);
+    } else if (pc.b <= 64) {
+      kern = (const void*)k_bulge_chase_smem<64>;
+      smem = 3 * 64 * 65 * sizeof(double);
+    }
+    if (smem > 48 * 1024) EVD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int maxG = max_coresident_blocks(kern, BC_NT, smem);
     int64_t G = n - 2;
     if (G > maxG) G = maxG;
     void* args[] = {&a};
     // model bytes (each step reads and writes its 2b x b window; U written once)
     const double nn = (double)n * (double)n;
     StatScope sc("bc_chase", s, 5.0 * pc.b * nn, 16.0 * pc.b * nn + (vectors ? 4.0 * nn : 0.0));
-    EVD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bulge_chase, dim3((unsigned)G), dim3(BC_NT), args, 0, s)); count_launch();
+    EVD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(BC_NT), args, smem, s)); count_launch();
   }
   if (n > 0) {
     k_extract_tridiag<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(w.band, pc.b, n, d, e); count_launch();

@@ -91,6 +91,57 @@ __global__ void k_scale(double* C, int64_t ldc, int64_t m, int64_t n, double bet
   }
 }
 
+// C (m x n, both <= 128) = alpha A^T B + beta C with a long K: partial products over
+// K chunks of 256 rows in FP64 (one CTA per chunk), then a fixed-order sum.
+constexpr int SK_CHUNK = 256;
+__global__ void __launch_bounds__(256) k_atb_partial(const double* __restrict__ A, int64_t lda,
+                                                     const double* __restrict__ B, int64_t ldb, int64_t m, int64_t n,
+                                                     int64_t k, double* part) {
+  __shared__ double As[32][129];
+  __shared__ double Bs[32][129];
+  const int64_t k0 = (int64_t)blockIdx.x * SK_CHUNK;
+  const int tid = threadIdx.x;
+  double acc[64];
+  const int nout = (int)(m * n);
+  for (int q = 0; q < 64; ++q) acc[q] = 0.0;
+  for (int64_t kk = k0; kk < k0 + SK_CHUNK && kk < k; kk += 32) {
+    __syncthreads();
+    for (int idx = tid; idx < 32 * 128; idx += 256) {
+      const int r = idx % 32, c = idx / 32;
+      const int64_t K = kk + r;
+      As[r][c] = (K < k && c < m) ? A[K + c * lda] : 0.0;
+      Bs[r][c] = (K < k && c < n) ? B[K + c * ldb] : 0.0;
+    }
+    __syncthreads();
+    for (int q = 0; q < 64; ++q) {
+      const int o = tid + q * 256;
+      if (o >= nout) break;
+      const int i = o % (int)m, j = o / (int)m;
+      double sacc = acc[q];
+      for (int r = 0; r < 32; ++r) sacc = fma(As[r][i], Bs[r][j], sacc);
+      acc[q] = sacc;
+    }
+  }
+  for (int q = 0; q < 64; ++q) {
+    const int o = tid + q * 256;
+    if (o >= nout) break;
+    part[(size_t)blockIdx.x * nout + o] = acc[q];
+  }
+}
+
+__global__ void k_atb_sum(const double* part, int nchunks, int64_t m, int64_t n, double alpha, double beta, double* C,
+                          int64_t ldc) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= m * n) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * m * n + o];
+  const int64_t i = o % m, j = o / m;
+  double* p = C + i + j * ldc;
+  double v = alpha * s;
+  if (beta != 0.0) v = fma(beta, *p, v);
+  *p = v;
+}
+
 }  // namespace
 
 size_t gemm_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
@@ -110,6 +161,19 @@ evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes
     return EVD_OK;
   }
   if (slices > 0 && (g.force_tc || ozaki_eligible(g))) return ozaki_gemm(g, slices, scratch, scratch_bytes, s);
+  // small A^T B with a long K: split K across CTAs
+  if (g.ta == 'T' && g.tb == 'N' && !g.lower && !g.a_sym_lower && g.m <= 128 && g.n <= 128 && g.m * g.n <= 64 * 256 &&
+      g.k >= 4 * SK_CHUNK && scratch) {
+    const int nch = (int)ceil_div(g.k, SK_CHUNK);
+    if (scratch_bytes >= (size_t)nch * g.m * g.n * sizeof(double)) {
+      StatScope sc("gemm_fp64_splitk", s, 2.0 * (double)g.m * (double)g.n * (double)g.k);
+      double* part = static_cast<double*>(scratch);
+      k_atb_partial<<<nch, 256, 0, s>>>(g.A, g.lda, g.B, g.ldb, g.m, g.n, g.k, part); count_launch();
+      k_atb_sum<<<(unsigned)ceil_div(g.m * g.n, 256), 256, 0, s>>>(part, nch, g.m, g.n, g.alpha, g.beta, g.C, g.ldc); count_launch();
+      EVD_CUDA_TRY(cudaGetLastError());
+      return EVD_OK;
+    }
+  }
   dim3 grid((unsigned)ceil_div(g.m, BM), (unsigned)ceil_div(g.n, BN));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
   const double flops = (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;

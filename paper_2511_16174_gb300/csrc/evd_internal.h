@@ -89,6 +89,7 @@ struct PlanCore {
   cudaStream_t stream = nullptr;
   int device = 0;
   int sms = 0;
+  int panel_ctas = 64;    // CTAs of the cooperative panel QR (EVD_PANEL_CTAS overrides)
   int* status = nullptr;  // device int[kStatusWords]
 };
 
@@ -134,6 +135,9 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
 
 struct BackWork {
   double* Tg;      // T factors of the BC reflector groups
+  double* Vg;      // V of the BC reflector groups of one sweep block (kmax x h x g)
+  double* Yg;      // Y = V T of the same groups
+  double* Wt;      // W^T (n x g)
   double* Vp;      // explicit V of an SBR panel block (n x nb)
   double* Wp;      // nb x n
   double* Tp;      // nb x nb

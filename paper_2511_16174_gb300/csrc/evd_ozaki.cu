@@ -7,8 +7,12 @@
 // A digit is an integer of at most 8 significant bits, so it is exact in bfloat16;
 // a product of two digits is exact in FP32.  The kernel forms, for every weight
 // k = t + u <= s-1, S_k = sum over pairs (t, u) and over K of sigma^A_t sigma^B_u with
-// tcgen05.mma kind::f16 into an FP32 accumulator in tensor memory.  An accumulator
-// drained every 256 K-elements never exceeds (k+3) 2^12 * 256 <= 2^24 in magnitude,
+// tcgen05.mma kind::f16 into an FP32 accumulator in tensor memory (64 columns per
+// weight, weight k at columns 64 k).  One instruction multiplies slice t of A by
+// up to four consecutive slices u0..u0+3 of B stacked along N (N <= 256), which
+// lands in the accumulators of weights t+u0..t+u0+3 -- 12 instructions per K-step
+// instead of 36.  The accumulators are drained every 256 K-elements; a weight-k
+// accumulator then never exceeds (k+3) 2^12 * 256 <= 2^24 in magnitude,
 // so every partial sum is an exact integer; drains are converted to int64 and
 // combined exactly, with left shifts only, into two accumulators
 //     R_hi = sum_{k <= H} S_k 2^(7 (H - k))      H = min(s-1, 3)
@@ -22,9 +26,8 @@
 //               slices (16 K-elements, 32-byte rows, 32-byte swizzle), 4 stages.
 //   warp 1      tensor-memory allocation (512 columns) and the single MMA-issuing
 //               thread: per stage, every slice pair (t, u) with t + u <= s-1.
-//   warps 2..9  epilogue: one accumulator per weight (64 columns each), drained on a
-//               staggered schedule (one weight every other stage) into int64
-//               registers, then the FP64 write of C.
+//   warps 2..9  epilogue: drains all weight accumulators every 16 stages into
+//               int64 registers, then the FP64 write of C.
 // Every mbarrier wait is bounded; on timeout the CTA raises the abort flag, sets
 // EVD_ERR_TIMEOUT in the status word and leaves after freeing tensor memory.
 #include <cuda.h>
@@ -50,6 +53,7 @@ constexpr int OZ_STAGES = 4;
 constexpr int OZ_THREADS = 320;
 constexpr int OZ_PERIOD = 16;     // stages between two drains of one weight (256 K-elements)
 constexpr long long OZ_WAIT_LIMIT = 1ll << 26;
+constexpr int OZ_GROUP_M = 8;     // row tiles per rasterization group
 
 // ------------------------------------------------------------------ operand views
 // Element (rho, kappa) of an operand seen as rows x K:
@@ -154,6 +158,55 @@ __global__ void k_split(const View v, const int* ex_biased, int* ex_frexp, int s
   }
 }
 
+// One-pass variant for short K (K <= 4096): each block owns 32 rows over the whole
+// K range, finds the row exponents, then writes the digits.  Saves the exponent
+// launch and the memset of the two-kernel path.
+__global__ void k_split_fused(const View v, int* ex_frexp, int s, int64_t rows_pad, int64_t K_pad,
+                              __nv_bfloat16* S) {
+  __shared__ double t[32][33];
+  __shared__ int red[8][32];
+  __shared__ int erow[32];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  int mx = 0;
+  for (int64_t k0 = 0; k0 < v.K; k0 += 32) {
+    __syncthreads();
+    load_tile32(v, r0, k0, t);
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(t[threadIdx.x][k]);
+      mx = max(mx, (int)((bits >> 52) & 0x7FF));
+    }
+  }
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    for (int y = 1; y < 8; ++y) mx = max(mx, red[y][threadIdx.x]);
+    const int e = (mx > 0) ? mx - 1022 : -1022;
+    erow[threadIdx.x] = e;
+    if (r0 + threadIdx.x < rows_pad) ex_frexp[r0 + threadIdx.x] = e;
+  }
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int q = tid & 15;
+  for (int64_t k0 = 0; k0 < K_pad; k0 += 32) {
+    __syncthreads();
+    load_tile32(v, r0, k0, t);
+    __syncthreads();
+    for (int rr = tid >> 4; rr < 32; rr += 16) {
+      const int64_t R = r0 + rr;
+      const int e = erow[rr];
+      int d0[OZ_MAXS], d1[OZ_MAXS];
+      ozaki_digits(t[rr][2 * q], e, s, d0);
+      ozaki_digits(t[rr][2 * q + 1], e, s, d1);
+      for (int tt = 0; tt < s; ++tt) {
+        __nv_bfloat162 h;
+        h.x = __float2bfloat16_rn((float)d0[tt]);
+        h.y = __float2bfloat16_rn((float)d1[tt]);
+        *reinterpret_cast<__nv_bfloat162*>(S + ((size_t)tt * rows_pad + R) * K_pad + k0 + 2 * q) = h;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -215,21 +268,6 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db
       "l"(da), "l"(db), "r"(idesc), "r"(acc)
       : "memory");
 }
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -240,6 +278,62 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// x 2^ex as a double, rounded to nearest even, from the signed 128-bit integer
+// (hi, lo) -- integer operations only (GB300's FP64 pipe is narrow).  Falls back to
+// FP64 arithmetic only when the result is subnormal or overflows.
+__device__ __forceinline__ double i128_to_double(long long hi, unsigned long long lo, int ex) {
+  const bool neg = hi < 0;
+  unsigned long long mh = (unsigned long long)hi, ml = lo;
+  if (neg) {  // two's complement negate
+    ml = ~ml + 1ull;
+    mh = ~mh + (ml == 0ull ? 1ull : 0ull);
+  }
+  if (mh == 0ull && ml == 0ull) return 0.0;
+  // position of the top bit
+  int p;
+  if (mh != 0ull) p = 127 - __clzll((long long)mh);
+  else p = 63 - __clzll((long long)ml);
+  unsigned long long m;
+  int E = p + ex;  // value = 1.xxx * 2^E
+  if (p <= 52) {
+    m = ml << (52 - p);
+  } else {
+    const int sh = p - 52;  // bits dropped below the 53-bit mantissa
+    // m = (mh:ml) >> sh, sticky and round bits
+    unsigned long long q, rem_hi, rem_lo;  // rem = dropped part
+    if (sh < 64) {
+      q = (ml >> sh) | (sh ? (mh << (64 - sh)) : 0ull);
+      rem_lo = sh ? (ml << (64 - sh)) : 0ull;  // dropped bits left-aligned
+      rem_hi = 0ull;
+      const unsigned long long half = 1ull << 63;
+      const bool round_up = (rem_lo > half) || (rem_lo == half && (q & 1ull));
+      m = q + (round_up ? 1ull : 0ull);
+      (void)rem_hi;
+    } else {
+      const int s2 = sh - 64;
+      q = mh >> s2;
+      // dropped bits, left-aligned in (d_hi, d_lo)
+      const unsigned long long d_hi = s2 ? ((mh << (64 - s2)) | (ml >> s2)) : ml;
+      const unsigned long long d_lo = s2 ? (ml << (64 - s2)) : 0ull;
+      const unsigned long long half = 1ull << 63;
+      const bool above = (d_hi > half) || (d_hi == half && d_lo != 0ull);
+      const bool tie = (d_hi == half && d_lo == 0ull);
+      const bool round_up = above || (tie && (q & 1ull));
+      m = q + (round_up ? 1ull : 0ull);
+    }
+    if (m >> 53) { m >>= 1; ++E; }
+  }
+  const int biased = E + 1023;
+  if (biased <= 0 || biased >= 2047) {
+    // rare: finish in FP64 arithmetic
+    double v = ldexp((double)(m & ((1ull << 53) - 1)), E - 52);
+    return neg ? -v : v;
+  }
+  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) |
+                                  (m & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
 }
 
 struct MmaArgs {
@@ -254,19 +348,32 @@ struct MmaArgs {
   double alpha, beta;
   int lower;
   int* st;
+  int stages_per_split;  // split K: CTA z handles stages [z * stages_per_split, ...)
+  double* part;          // split K: partial products (alpha = 1, beta = 0), m x n each, ld m
 };
 
-__device__ __forceinline__ bool drain_after(int j, int k, int nst) {
-  return ((j + 2 * k) % OZ_PERIOD == OZ_PERIOD - 1) || (j == nst - 1);
+__device__ __forceinline__ bool drain_after(int j, int nst) {
+  return (j % OZ_PERIOD == OZ_PERIOD - 1) || (j == nst - 1);
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const MmaArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  const int64_t m0 = (int64_t)blockIdx.x * OZ_BM, n0 = (int64_t)blockIdx.y * OZ_BN;
+  // grouped rasterization: consecutive CTAs sweep OZ_GROUP_M row tiles for each
+  // column tile, so a wave shares both operands' slices in L2
+  const int num_m = (int)gridDim.x, num_n = (int)gridDim.y;
+  const int id = (int)(blockIdx.x + (int64_t)blockIdx.y * gridDim.x);
+  const int group = id / (OZ_GROUP_M * num_n);
+  const int first_m = group * OZ_GROUP_M;
+  const int gm = (num_m - first_m < OZ_GROUP_M) ? num_m - first_m : OZ_GROUP_M;
+  const int in_group = id - group * OZ_GROUP_M * num_n;
+  const int mt = first_m + in_group % gm, nt = in_group / gm;
+  const int64_t m0 = (int64_t)mt * OZ_BM, n0 = (int64_t)nt * OZ_BN;
   if (a.lower && n0 > m0 + OZ_BM - 1) return;  // tile strictly above the diagonal
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int s = a.s, L = s - 1;
+  const int j0 = (int)blockIdx.z * a.stages_per_split;
+  const int nst = (a.nst - j0 < a.stages_per_split) ? a.nst - j0 : a.stages_per_split;
   const uint32_t a_bytes = (uint32_t)s * OZ_BM * OZ_KS * 2, b_bytes = (uint32_t)s * OZ_BN * OZ_KS * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * stage_bytes);
@@ -280,7 +387,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < OZ_STAGES; ++i) { mbar_init(smem_u32(full + i), 1); mbar_init(smem_u32(empty + i), 1); }
-    for (int k = 0; k < OZ_MAXS; ++k) { mbar_init(smem_u32(accf + k), 1); mbar_init(smem_u32(acce + k), 8); }
+    mbar_init(smem_u32(accf), 1);
+    mbar_init(smem_u32(acce), 8);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -300,14 +408,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
       int issued = 0;
-      for (int j = 0; j < a.nst; ++j) {
+      for (int j = 0; j < nst; ++j) {
         const int si = j % OZ_STAGES, round = j / OZ_STAGES;
         if (round > 0 && !mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9001)) break;
         uint8_t* sa = smem + si * stage_bytes;
         const uint32_t fb = smem_u32(full + si);
         mbar_expect_tx(fb, stage_bytes);
-        tma_load_3d(smem_u32(sa), &tmA, j * OZ_KS, (int)m0, 0, fb);
-        tma_load_3d(smem_u32(sa + a_bytes), &tmB, j * OZ_KS, (int)n0, 0, fb);
+        tma_load_3d(smem_u32(sa), &tmA, (j0 + j) * OZ_KS, (int)m0, 0, fb);
+        tma_load_3d(smem_u32(sa + a_bytes), &tmB, (j0 + j) * OZ_KS, (int)n0, 0, fb);
         ++issued;
       }
       if (*abort) {
@@ -321,33 +429,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                             ((uint32_t)(OZ_BM >> 4) << 24);
-      int chunks[OZ_MAXS];
-      for (int k = 0; k < OZ_MAXS; ++k) chunks[k] = 0;
-      for (int j = 0; j < a.nst && !*abort; ++j) {
+      uint32_t idesc[4];
+      for (int q = 0; q < 4; ++q)
+        idesc[q] = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((OZ_BN * (q + 1)) >> 3) << 17) |
+                   ((uint32_t)(OZ_BM >> 4) << 24);
+      int chunk = 0;
+      for (int j = 0; j < nst && !*abort; ++j) {
         const int si = j % OZ_STAGES, round = j / OZ_STAGES;
         if (!mbar_wait(smem_u32(full + si), round & 1, abort, a.st, 9002)) break;
         tc_fence_after();
+        const bool fresh = (j % OZ_PERIOD) == 0;
+        if (fresh && j > 0) {
+          if (!mbar_wait(smem_u32(acce), (chunk - 1) & 1, abort, a.st, 9003)) break;
+          tc_fence_after();
+        }
         const uint32_t sa = smem_u32(smem + si * stage_bytes);
         const uint32_t sb = sa + a_bytes;
-        for (int k = 0; k <= L; ++k) {
-          const bool fresh = (j == 0) || drain_after(j - 1, k, a.nst);
-          if (fresh && chunks[k] > 0) {
-            if (!mbar_wait(smem_u32(acce + k), (chunks[k] - 1) & 1, abort, a.st, 9003)) break;
-            tc_fence_after();
+        for (int t = 0; t <= L; ++t) {
+          const int nu = L - t + 1;  // u = 0 .. L - t
+          const uint64_t da = desc_sw32(sa + (uint32_t)t * OZ_BM * OZ_KS * 2);
+          for (int u0 = 0; u0 < nu; u0 += 4) {
+            const int cnt = (nu - u0 < 4) ? nu - u0 : 4;
+            const uint64_t db = desc_sw32(sb + (uint32_t)u0 * OZ_BN * OZ_KS * 2);
+            tc_mma(tmem + (uint32_t)((t + u0) * OZ_BN), da, db, idesc[cnt - 1], (fresh && t == 0) ? 0u : 1u);
           }
-          const int tlo = (k - L > 0) ? k - L : 0, thi = (k < L) ? k : L;
-          for (int t = tlo; t <= thi; ++t) {
-            const int u = k - t;
-            const uint64_t da = desc_sw32(sa + (uint32_t)t * OZ_BM * OZ_KS * 2);
-            const uint64_t db = desc_sw32(sb + (uint32_t)u * OZ_BN * OZ_KS * 2);
-            tc_mma(tmem + (uint32_t)(k * OZ_BN), da, db, idesc, (fresh && t == tlo) ? 0u : 1u);
-          }
-          if (drain_after(j, k, a.nst)) {
-            tc_commit(smem_u32(accf + k));
-            ++chunks[k];
-          }
+        }
+        if (drain_after(j, nst)) {
+          tc_commit(smem_u32(accf));
+          ++chunk;
         }
         tc_commit(smem_u32(empty + si));
       }
@@ -360,15 +469,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     long long Rh[32], Rl[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) { Rh[c] = 0; Rl[c] = 0; }
-    int drains[OZ_MAXS];
-    for (int k = 0; k < OZ_MAXS; ++k) drains[k] = 0;
     bool ok = true;
-    for (int j = 0; j < a.nst && ok; ++j) {
+    int chunk = 0;
+    for (int j = 0; j < nst && ok; ++j) {
+      if (!drain_after(j, nst)) continue;
+      if (!mbar_wait(smem_u32(accf), chunk & 1, abort, a.st, 9004)) { ok = false; break; }
+      ++chunk;
+      tc_fence_after();
       for (int k = 0; k <= L; ++k) {
-        if (!drain_after(j, k, a.nst)) continue;
-        if (!mbar_wait(smem_u32(accf + k), drains[k] & 1, abort, a.st, 9004)) { ok = false; break; }
-        ++drains[k];
-        tc_fence_after();
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + half * 32);
         const bool hi = (k <= 3);
         const int sh = hi ? 7 * (H - k) : 7 * (L - k);
@@ -384,24 +492,39 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int c = 0; c < 16; ++c) Rl[16 * h + c] += (long long)__float2int_rn(v[c]) << sh;
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(acce + k));
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(acce));
     }
     if (ok && row < a.m) {
       const int er = a.ea[row];
+      const int shift_hi = 7 * (L - H);  // R = R_hi 2^(7 (L - H)) + R_lo, value R 2^(e_r + f_c - 14 - 7L)
+      const bool alpha_one = (a.alpha == 1.0), alpha_mone = (a.alpha == -1.0);
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int64_t col = n0 + half * 32 + c;
         if (col < a.n && !(a.lower && row < col)) {
-          const int ex = er + a.eb[col] - 14;
-          double v = ldexp((double)Rh[c], ex - 7 * H);
-          if (L >= 4) v += ldexp((double)Rl[c], ex - 7 * L);
-          v *= a.alpha;
-          double* p = a.C + row + col * a.ldc;
-          if (a.beta != 0.0) v = fma(a.beta, *p, v);
-          *p = v;
+          // exact 128-bit R = Rh << shift_hi + Rl
+          const long long rh = Rh[c];
+          unsigned long long lo = (shift_hi == 0) ? (unsigned long long)rh : ((unsigned long long)rh << shift_hi);
+          long long hi = (shift_hi == 0) ? (rh >> 63) : (rh >> (64 - shift_hi));
+          if (L >= 4) {
+            const long long rl = Rl[c];
+            const unsigned long long nlo = lo + (unsigned long long)rl;
+            hi += (rl >> 63) + (nlo < lo ? 1 : 0);
+            lo = nlo;
+          }
+          double v = i128_to_double(hi, lo, er + a.eb[col] - 14 - 7 * L);
+          if (a.part) {
+            a.part[(size_t)blockIdx.z * a.m * a.n + row + col * a.m] = v;
+          } else {
+            if (alpha_mone) v = -v;
+            else if (!alpha_one) v *= a.alpha;
+            double* p = a.C + row + col * a.ldc;
+            if (a.beta != 0.0) v = (a.beta == 1.0) ? (*p + v) : fma(a.beta, *p, v);
+            *p = v;
+          }
         }
       }
     }
@@ -411,6 +534,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+// C = alpha sum_z part_z + beta C (split K), fixed summation order.
+__global__ void k_splitk_reduce(const double* part, int splits, int64_t m, int64_t n, double alpha, double beta,
+                                double* C, int64_t ldc, int lower) {
+  const int64_t j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (lower && i < j) continue;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * m * n + i + j * m];
+    double* p = C + i + j * ldc;
+    double v = alpha * s;
+    if (beta != 0.0) v = fma(beta, *p, v);
+    *p = v;
   }
 }
 
@@ -447,6 +585,22 @@ Pads pads(int64_t m, int64_t n, int64_t k) {
   return {ceil_div(m, OZ_BM) * OZ_BM, ceil_div(n, OZ_BN) * OZ_BN, ceil_div(k, 32) * 32};
 }
 
+// split K when the tile grid cannot fill the GPU: returns the split count
+int splitk_count(int64_t m, int64_t n, int64_t k) {
+  const int64_t tiles = ceil_div(m, OZ_BM) * ceil_div(n, OZ_BN);
+  const int64_t k_pad = ceil_div(k, 32) * 32;
+  int sms = 152;
+  if (tiles >= sms || k_pad < 1024) return 1;
+  int64_t sp = ceil_div(sms, tiles);
+  sp = std::min<int64_t>(sp, k_pad / 512);
+  if (m * n * sp > ((int64_t)1 << 27)) sp = std::max<int64_t>(1, ((int64_t)1 << 27) / (m * n));
+  return (int)std::max<int64_t>(sp, 1);
+}
+size_t splitk_bytes(int64_t m, int64_t n, int64_t k) {
+  const int sp = splitk_count(m, n, k);
+  return sp > 1 ? (size_t)sp * m * n * sizeof(double) : 0;
+}
+
 size_t smem_bytes(int s) {
   return 1024 + (size_t)OZ_STAGES * s * (OZ_BM + OZ_BN) * OZ_KS * 2 + (2 * OZ_STAGES + 2 * OZ_MAXS) * 8 + 16;
 }
@@ -463,6 +617,7 @@ size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
   c.take<int>((size_t)p.n_pad);
   c.take<int>((size_t)p.m_pad);
   c.take<int>((size_t)p.n_pad);
+  c.take<double>(splitk_bytes(m, n, k) / sizeof(double));
   return c.off + 256;
 }
 
@@ -484,6 +639,8 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
   int* exB = c.take<int>((size_t)p.n_pad);
   int* eA = c.take<int>((size_t)p.m_pad);
   int* eB = c.take<int>((size_t)p.n_pad);
+  const int splits = splitk_count(g.m, g.n, g.k);
+  double* part = c.take<double>(splitk_bytes(g.m, g.n, g.k) / sizeof(double));
   View va, vb;
   va.p = g.A; va.ld = g.lda; va.rows = g.m; va.K = g.k;
   va.mode = g.a_sym_lower ? 2 : (g.ta == 'N' ? 0 : 1);
@@ -493,16 +650,21 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
   {
     StatScope sc("gemm_tc_split_prep", s, 0.0,
                  8.0 * (double)(g.m + g.n) * (double)g.k * 2.0 + 2.0 * slices * (double)(p.m_pad + p.n_pad) * p.k_pad);
-    EVD_CUDA_TRY(cudaMemsetAsync(exA, 0, sizeof(int) * p.m_pad, s));
-    EVD_CUDA_TRY(cudaMemsetAsync(exB, 0, sizeof(int) * p.n_pad, s));
-    const int64_t kspan = 1024;
     dim3 blk(32, 8);
-    k_row_exponent<<<dim3((unsigned)ceil_div(g.m, 32), (unsigned)ceil_div(g.k, kspan)), blk, 0, s>>>(va, exA, kspan); count_launch();
-    k_row_exponent<<<dim3((unsigned)ceil_div(g.n, 32), (unsigned)ceil_div(g.k, kspan)), blk, 0, s>>>(vb, exB, kspan); count_launch();
-    k_split<<<dim3((unsigned)(p.m_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(va, exA, eA, slices, p.m_pad,
-                                                                                   p.k_pad, SA); count_launch();
-    k_split<<<dim3((unsigned)(p.n_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(vb, exB, eB, slices, p.n_pad,
-                                                                                   p.k_pad, SB); count_launch();
+    if (p.k_pad <= 512) {
+      k_split_fused<<<(unsigned)(p.m_pad / 32), blk, 0, s>>>(va, eA, slices, p.m_pad, p.k_pad, SA); count_launch();
+      k_split_fused<<<(unsigned)(p.n_pad / 32), blk, 0, s>>>(vb, eB, slices, p.n_pad, p.k_pad, SB); count_launch();
+    } else {
+      EVD_CUDA_TRY(cudaMemsetAsync(exA, 0, sizeof(int) * p.m_pad, s));
+      EVD_CUDA_TRY(cudaMemsetAsync(exB, 0, sizeof(int) * p.n_pad, s));
+      const int64_t kspan = 1024;
+      k_row_exponent<<<dim3((unsigned)ceil_div(g.m, 32), (unsigned)ceil_div(g.k, kspan)), blk, 0, s>>>(va, exA, kspan); count_launch();
+      k_row_exponent<<<dim3((unsigned)ceil_div(g.n, 32), (unsigned)ceil_div(g.k, kspan)), blk, 0, s>>>(vb, exB, kspan); count_launch();
+      k_split<<<dim3((unsigned)(p.m_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(va, exA, eA, slices, p.m_pad,
+                                                                                     p.k_pad, SA); count_launch();
+      k_split<<<dim3((unsigned)(p.n_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(vb, exB, eB, slices, p.n_pad,
+                                                                                     p.k_pad, SB); count_launch();
+    }
     EVD_CUDA_TRY(cudaGetLastError());
   }
   CUtensorMap tmA, tmB;
@@ -515,6 +677,13 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
   a.tmem_cols = cols;
   a.ea = eA; a.eb = eB; a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha; a.beta = g.beta;
   a.lower = g.lower ? 1 : 0; a.st = nullptr;
+  {
+    // stages per split: a multiple of the drain period so chunks stay aligned
+    const int per = (int)ceil_div(ceil_div(a.nst, splits), OZ_PERIOD) * OZ_PERIOD;
+    a.stages_per_split = per;
+  }
+  const int zsplits = (int)ceil_div(a.nst, a.stages_per_split);
+  a.part = (zsplits > 1) ? part : nullptr;
   static int* d_dummy_status = nullptr;  // status word for timeouts of standalone products
   if (!d_dummy_status) {
     if (cudaMalloc(&d_dummy_status, sizeof(int) * kStatusWords) != cudaSuccess) return EVD_ERR_OOM;
@@ -528,11 +697,19 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
                                       (int)smem_bytes(OZ_MAXS)));
     attr_set = true;
   }
-  dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN));
+  dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)zsplits);
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
   StatScope sc("gemm_tc_split", s, flops * (double)(slices * (slices + 1) / 2));
   k_ozaki_mma<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, a); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
+  if (zsplits > 1) {
+    for (int64_t j0 = 0; j0 < g.n; j0 += 65535) {
+      const int64_t cols = std::min<int64_t>(g.n - j0, 65535);
+      k_splitk_reduce<<<dim3((unsigned)std::min<int64_t>(ceil_div(g.m, 256), 16), (unsigned)cols), 256, 0, s>>>(
+          part + j0 * g.m, zsplits, g.m, g.n, g.alpha, g.beta, g.C + j0 * g.ldc, g.ldc, g.lower ? 1 : 0); count_launch();
+    }
+    EVD_CUDA_TRY(cudaGetLastError());
+  }
   return EVD_OK;
 }
 

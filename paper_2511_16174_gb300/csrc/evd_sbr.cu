@@ -69,9 +69,12 @@ __global__ void __launch_bounds__(PQ_NT) k_panel_qr(const PanelArgs a) {
     double* nxt = (i & 1) ? part0 : part1;
     if (!grid_barrier(a.bar, G, a.st, 100 + i)) return;
     // ---- reflector for column i (every CTA computes the same scalars)
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // the per-CTA partial norms, summed by one warp (lanes load in parallel)
       double ss = 0.0;
-      for (unsigned q = 0; q < G; ++q) ss += __ldcg(cur + (size_t)q * stride);
+      for (unsigned q = threadIdx.x; q < G; q += 32) ss += __ldcg(cur + (size_t)q * stride);
+      ss = warp_sum(ss);
+      if (threadIdx.x == 0) {
       double alpha = __ldcg(a.P + i + (int64_t)i * a.lda);
       double tau = 0.0, beta = alpha, scale = 0.0;
       if (ss != 0.0) {
@@ -81,6 +84,7 @@ __global__ void __launch_bounds__(PQ_NT) k_panel_qr(const PanelArgs a) {
         scale = 1.0 / (alpha - beta);
       }
       sh_par[0] = tau; sh_par[1] = beta; sh_par[2] = scale;
+      }
     }
     __syncthreads();
     const double tau = sh_par[0], scale = sh_par[2];
@@ -93,20 +97,27 @@ __global__ void __launch_bounds__(PQ_NT) k_panel_qr(const PanelArgs a) {
       a.V[r + (int64_t)i * a.ldv] = v;
     }
     __syncthreads();
-    // partial dots y_j = v^T P(:, j) for j > i over own rows (r >= i)
-    for (int j = i + 1; j < a.bw; ++j) {
-      const double* pj = a.P + (int64_t)j * a.lda;
-      double s = 0.0;
-      for (int64_t r = (rb > i ? rb : i) + threadIdx.x; r < re; r += PQ_NT)
-        s += a.V[r + (int64_t)i * a.ldv] * pj[r];
-      s = block_sum<PQ_NT>(s, red);
-      if (threadIdx.x == 0) cur[(size_t)g * stride + 1 + j] = s;
+    // partial dots y_j = v^T P(:, j) for j > i over own rows (r >= i), one warp per column
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int j = i + 1 + warp; j < a.bw; j += PQ_NT / 32) {
+        const double* pj = a.P + (int64_t)j * a.lda;
+        double s = 0.0;
+        for (int64_t r = (rb > i ? rb : i) + lane; r < re; r += 32) s += a.V[r + (int64_t)i * a.ldv] * pj[r];
+        s = warp_sum(s);
+        if (lane == 0) cur[(size_t)g * stride + 1 + j] = s;
+      }
     }
     if (!grid_barrier(a.bar, G, a.st, 200 + i)) return;
-    for (int j = i + 1 + threadIdx.x; j < a.bw; j += PQ_NT) {
-      double s = 0.0;
-      for (unsigned q = 0; q < G; ++q) s += __ldcg(cur + (size_t)q * stride + 1 + j);
-      sh_y[j] = s;
+    {
+      // y_j = sum of the per-CTA partials, one warp per column
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int j = i + 1 + warp; j < a.bw; j += PQ_NT / 32) {
+        double s = 0.0;
+        for (unsigned q = lane; q < G; q += 32) s += __ldcg(cur + (size_t)q * stride + 1 + j);
+        s = warp_sum(s);
+        if (lane == 0) sh_y[j] = s;
+      }
     }
     __syncthreads();
     // update own rows of the remaining columns
@@ -122,12 +133,12 @@ __global__ void __launch_bounds__(PQ_NT) k_panel_qr(const PanelArgs a) {
     }
     // norm^2 of the next column below its diagonal (rows updated above by other threads)
     __syncthreads();
-    if (i + 1 < a.kb) {
+    if (i + 1 < a.kb && threadIdx.x < 32) {
       const double* pn = a.P + (int64_t)(i + 1) * a.lda;
       double ss = 0.0;
-      for (int64_t r = rb + threadIdx.x; r < re; r += PQ_NT)
+      for (int64_t r = rb + threadIdx.x; r < re; r += 32)
         if (r > i + 1) { double x = pn[r]; ss += x * x; }
-      ss = block_sum<PQ_NT>(ss, red);
+      ss = warp_sum(ss);
       if (threadIdx.x == 0) nxt[(size_t)g * stride] = ss;
     }
   }
@@ -219,6 +230,7 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
     pa.T = w.T + (size_t)p * b * b;
     pa.partial = w.partial; pa.bar = w.bar; pa.st = pc.status;
     int G = (int)ceil_div(m, 64);
+    if (G > pc.panel_ctas) G = pc.panel_ctas;  // barrier cost grows with the CTA count
     if (G > maxG) G = maxG;
     if (G < 1) G = 1;
     EVD_CUDA_TRY(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
@@ -237,7 +249,7 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
     g2.status = pc.status;
     g2.ta = 'T'; g2.m = kb; g2.n = kb; g2.k = m; g2.A = w.W; g2.lda = n; g2.B = w.Y; g2.ldb = n;
     g2.C = w.M; g2.ldc = b; g2.alpha = 1.0; g2.beta = 0.0;
-    st = gemm(g2, 0, nullptr, 0, s);
+    st = gemm(g2, 0, w.gemm_ws, w.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
     EVD_CUDA_TRY(cudaMemcpy2DAsync(w.Z, n * sizeof(double), w.Y, n * sizeof(double), m * sizeof(double), kb,
                                    cudaMemcpyDeviceToDevice, s));

@@ -222,7 +222,7 @@ def ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     evd.stats_reset()
-    evd.stats_enable(True)
+    evd.stats_enable(not args.no_stats)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -360,6 +360,7 @@ def main():
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-stats", action="store_true", help="no per-category event timing in the timed region")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

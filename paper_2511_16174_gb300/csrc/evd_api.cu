@@ -52,14 +52,17 @@ int64_t n_panels(int64_t n, int b) {
 
 constexpr int kMaxPanelCtas = 2048;
 
-size_t sbr_union_bytes(int64_t n, int b) {
+size_t sbr_union_bytes(int64_t n, int b, int nb) {
   Carver c(nullptr);
   c.take<double>((size_t)n * b);  // V
   c.take<double>((size_t)n * b);  // W
   c.take<double>((size_t)n * b);  // Z
   c.take<double>((size_t)n * b);  // Y
   c.take<double>((size_t)b * b * 4);
-  c.take<double>((size_t)2 * kMaxPanelCtas * (1 + b) + (size_t)b * b);
+  c.take<double>((size_t)2 * kMaxPanelCtas * (2 + b) + (size_t)b * b);
+  c.take<double>((size_t)n * 2 * nb);  // VZ
+  c.take<double>((size_t)n * 2 * nb);  // ZV
+  c.take<double>((size_t)2 * nb * nb); // X
   return c.off;
 }
 size_t dc_union_bytes(int64_t n) {
@@ -108,7 +111,7 @@ WsLayout make_layout(const PlanCore& pc, void* ws) {
     L.Qd_int = c.take<double>((size_t)n * n);
   }
   if (pc.prec == EVD_SPLIT_BF16) L.A0 = c.take<double>((size_t)n * n);
-  size_t ub = std::max({sbr_union_bytes(n, b), dc_union_bytes(n), back_union_bytes(n, b),
+  size_t ub = std::max({sbr_union_bytes(n, b, pc.nb), dc_union_bytes(n), back_union_bytes(n, b),
                         pc.prec == EVD_SPLIT_BF16 ? refine_union_bytes(n) : (size_t)0});
   L.uni = c.take<char>(ub);
   L.uni_bytes = ub;
@@ -132,7 +135,10 @@ SbrWork sbr_work(const evd_plan_s* p, const WsLayout& L) {
   w.Z = c.take<double>((size_t)n * b);
   w.Y = c.take<double>((size_t)n * b);
   w.M = c.take<double>((size_t)b * b * 4);
-  w.partial = c.take<double>((size_t)2 * kMaxPanelCtas * (1 + b) + (size_t)b * b);
+  w.partial = c.take<double>((size_t)2 * kMaxPanelCtas * (2 + b) + (size_t)b * b);
+  w.VZ = c.take<double>((size_t)n * 2 * p->core.nb);
+  w.ZV = c.take<double>((size_t)n * 2 * p->core.nb);
+  w.X = c.take<double>((size_t)2 * p->core.nb * p->core.nb);
   w.bar = p->d_bar;
   w.band = L.band;
   w.gemm_ws = L.gemm_ws;

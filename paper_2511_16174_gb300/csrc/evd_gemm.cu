@@ -177,7 +177,7 @@ evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes
   dim3 grid((unsigned)ceil_div(g.m, BM), (unsigned)ceil_div(g.n, BN));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
   const double flops = (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;
-  StatScope sc("gemm_fp64_simt", s, flops);
+  StatScope sc(g.tag ? g.tag : "gemm_fp64_simt", s, flops);
   k_dgemm_simt<<<grid, NT, 0, s>>>(g); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   return EVD_OK;

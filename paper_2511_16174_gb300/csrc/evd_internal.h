@@ -69,6 +69,8 @@ struct Gemm {
   int* status = nullptr;
   // use the tensor-core product whenever slices > 0 (stand-alone requests)
   bool force_tc = false;
+  // statistics category of this product (nullptr: by engine)
+  const char* tag = nullptr;
 };
 
 // Scratch a product needs (bytes) and the call itself.
@@ -102,6 +104,9 @@ struct SbrWork {
   double* Z;       // n * nb
   double* Y;       // n * nb            (scratch, A2 W)
   double* M;       // nb * nb * 4       (small products)
+  double* VZ;      // n x 2 nb: [V_0 Z_0 V_1 Z_1 ...] of the current block
+  double* ZV;      // n x 2 nb: [Z_0 V_0 Z_1 V_1 ...]
+  double* X;       // 2 nb x nb
   double* partial; // per-CTA partial sums of the panel kernel
   unsigned* bar;   // grid barrier words
   double* band;    // (2b+1) x n lower band with room for the bulge

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "device_util.cuh"
 #include "evd_ozaki.h"
@@ -566,7 +567,37 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 3-D map over S[s][rows_pad][K_pad] (bf16), box {16, box_rows, s}, 32-byte swizzle.
+// Encoded maps are cached by (base, extents, box): the slice buffers of a plan's
+// workspace are reused call after call, and encoding is a host-side cost.
+struct MapKey {
+  void* base;
+  int64_t K_pad, rows_pad;
+  int s, box_rows;
+};
+constexpr int kMapCache = 64;
+MapKey g_map_keys[kMapCache];
+CUtensorMap g_maps[kMapCache];
+int g_map_n = 0, g_map_next = 0;
+std::mutex g_map_mu;
+
+bool make_map_uncached(CUtensorMap* tm, void* base, int64_t K_pad, int64_t rows_pad, int s, int box_rows);
 bool make_map(CUtensorMap* tm, void* base, int64_t K_pad, int64_t rows_pad, int s, int box_rows) {
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  for (int i = 0; i < g_map_n; ++i) {
+    const MapKey& k = g_map_keys[i];
+    if (k.base == base && k.K_pad == K_pad && k.rows_pad == rows_pad && k.s == s && k.box_rows == box_rows) {
+      *tm = g_maps[i];
+      return true;
+    }
+  }
+  if (!make_map_uncached(tm, base, K_pad, rows_pad, s, box_rows)) return false;
+  const int slot = (g_map_n < kMapCache) ? g_map_n++ : (g_map_next++ % kMapCache);
+  g_map_keys[slot] = {base, K_pad, rows_pad, s, box_rows};
+  g_maps[slot] = *tm;
+  return true;
+}
+
+bool make_map_uncached(CUtensorMap* tm, void* base, int64_t K_pad, int64_t rows_pad, int s, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)K_pad, (cuuint64_t)rows_pad, (cuuint64_t)s};
@@ -699,7 +730,7 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
   }
   dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)zsplits);
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
-  StatScope sc("gemm_tc_split", s, flops * (double)(slices * (slices + 1) / 2));
+  StatScope sc(g.tag ? g.tag : "gemm_tc_split", s, flops * (double)(slices * (slices + 1) / 2));
   k_ozaki_mma<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, a); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   if (zsplits > 1) {

@@ -44,11 +44,13 @@ def norm2(A):
     return float(np.max(np.abs(np.linalg.eigvalsh(A)))) if A.shape[0] else 0.0
 
 
-@pytest.mark.parametrize("n,b", [(64, 8), (100, 32), (257, 32), (512, 32), (300, 64)])
-def test_sbr_band_matches_oracle(evd, n, b):
+@pytest.mark.parametrize("n,b,nb", [(64, 8, 8), (100, 32, 32), (257, 32, 32), (512, 32, 32), (300, 64, 64),
+                                    (257, 32, 64), (512, 32, 128), (300, 16, 64), (129, 8, 32), (1000, 64, 256)])
+def test_sbr_band_matches_oracle(evd, n, b, nb):
+    """Double blocking (nb > b) defers the trailing update but computes the same band."""
     A = inputs.goe(n, 1000 + n + b)
     B_ref, _, _ = oracle.sbr(A, b)
-    plan = evd.Plan(n, job="V", b=b, nb=b)
+    plan = evd.Plan(n, job="V", b=b, nb=nb)
     ws = plan.workspace()
     Ad = to_dev(A)
     plan.sbr(Ad, ws)
@@ -160,11 +162,12 @@ def test_syevd_values_n512_goe(evd):
     _check_full(A, to_host(w), None, w_ref=w_ref)
 
 
-@pytest.mark.parametrize("n,b", [(100, 8), (300, 32), (1024, 64), (777, 32)])
-def test_syevd_vectors(evd, n, b):
+@pytest.mark.parametrize("n,b,nb", [(100, 8, 8), (300, 32, 32), (1024, 64, 64), (777, 32, 32), (1100, 32, 128),
+                                    (2100, 64, 128)])
+def test_syevd_vectors(evd, n, b, nb):
     A = inputs.goe(n, 4000 + n)
     w_ref, Q_ref = oracle.eigh(A)
-    w, Q = evd.syevd(to_dev(A), job="V", b=b, nb=b)
+    w, Q = evd.syevd(to_dev(A), job="V", b=b, nb=nb)
     _check_full(A, to_host(w), to_host(Q), w_ref=w_ref)
 
 

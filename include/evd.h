@@ -152,6 +152,29 @@ evd_status_t evd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k
                        double* C, int64_t ldc, int slices, void* ws, size_t ws_bytes,
                        void* stream);
 
+/* ---------------------------------------------------------------------------
+ * evd_dgemm without a workspace: the same product as evd_dgemm, with the same
+ * arguments minus ws/ws_bytes.  The paper has no counterpart.  It serves callers
+ * that cannot allocate device memory or pass a workspace through: a C host with no
+ * device allocator, a callback with a fixed signature, or code that must avoid
+ * cudaMalloc/cudaFree because they act on the whole device.
+ *
+ * The scratch is one fixed array in device global memory, EVD_STATIC_SCRATCH_BYTES
+ * per device, owned by the library.  The call allocates nothing.  Rules:
+ * - A product whose evd_gemm_workspace_size() exceeds EVD_STATIC_SCRATCH_BYTES
+ *   returns EVD_ERR_WORKSPACE at once, with no device work.
+ * - Calls that overlap in time race on the shared array: calls on different
+ *   streams, or from different host threads, must not be in flight together.
+ *   Calls queued one after another on the same stream are safe.
+ * - The first call on each device looks up the array's device address, which
+ *   may load the module.  Make that first call outside any stream capture.
+ * Errors: as evd_dgemm; a lookup failure returns EVD_ERR_CUDA. */
+#define EVD_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+evd_status_t evd_dgemm_static(char transa, char transb, int64_t m, int64_t n, int64_t k,
+                              double alpha, const double* A, int64_t lda, const double* B,
+                              int64_t ldb, double beta, double* C, int64_t ldc, int slices,
+                              void* stream);
+
 /* Autotuner: time candidate (b, nb) in {32, 64, 128}^2, nb >= b, for an n x n
  * problem and cache the winner in the JSON file at cache_path (NULL = no cache).
  * Allocates its own scratch with cudaMalloc.  Returns the choice in *b, *nb. */

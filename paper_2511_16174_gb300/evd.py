@@ -50,6 +50,8 @@ _SIGS = {
     "evd_gemm_workspace_size": ([_i64, _i64, _i64, _int, ctypes.POINTER(_sz)], _int),
     "evd_dgemm": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64,
                    _int, _vp, _sz, _vp], _int),
+    "evd_dgemm_static": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp,
+                          _i64, _int, _vp], _int),
     "evd_autotune": ([_i64, _int, _int, ctypes.c_char_p, ctypes.POINTER(_int), ctypes.POINTER(_int)], _int),
     "evd_stats_enable": ([_int], None),
     "evd_stats_reset": ([], None),
@@ -206,6 +208,17 @@ def dgemm(transa, transb, alpha, A, B, beta, C, slices=8, stream=None):
     _check(_lib.evd_dgemm(transa.encode(), transb.encode(), m, n, k, float(alpha), _ptr(A), _ld(A), _ptr(B), _ld(B),
                           float(beta), _ptr(C), _ld(C), int(slices), _ptr(ws), sz.value, _stream_ptr(stream)),
            "evd_dgemm")
+    return C
+
+
+def dgemm_static(transa, transb, alpha, A, B, beta, C, slices=8, stream=None):
+    """C = alpha op(A) op(B) + beta C through evd_dgemm_static (library-owned scratch,
+    no workspace argument; see include/evd.h for its size limit and ordering rule)."""
+    m, n = C.shape
+    k = A.shape[1] if transa == "N" else A.shape[0]
+    _check(_lib.evd_dgemm_static(transa.encode(), transb.encode(), m, n, k, float(alpha), _ptr(A), _ld(A), _ptr(B),
+                                 _ld(B), float(beta), _ptr(C), _ld(C), int(slices), _stream_ptr(stream)),
+           "evd_dgemm_static")
     return C
 
 

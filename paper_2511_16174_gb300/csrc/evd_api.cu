@@ -79,10 +79,10 @@ size_t back_union_bytes(int64_t n, int b) {
   c.take<double>((size_t)n * b);
   c.take<double>((size_t)n * b);
   c.take<double>((size_t)n * b);
-  const int64_t kmax = n / b + 2, h = 2 * b - 1;
-  c.take<double>((size_t)kmax * h * b);
-  c.take<double>((size_t)kmax * h * b);
-  c.take<double>((size_t)n * b);
+  const int64_t pmax = bc_wave_max_groups(n, b), h = 2 * b - 1;
+  c.take<double>((size_t)pmax * h * b);
+  c.take<double>((size_t)pmax * h * b);
+  c.take<double>((size_t)pmax * n * b);
   return c.off;
 }
 size_t refine_union_bytes(int64_t n) {
@@ -180,10 +180,12 @@ BackWork back_work(const evd_plan_s* p, const WsLayout& L) {
   w.Vp = c.take<double>((size_t)n * b);
   w.Wp = c.take<double>((size_t)n * b);
   w.Tp = c.take<double>((size_t)n * b);
-  const int64_t kmax = n / b + 2, h = 2 * b - 1;
-  w.Vg = c.take<double>((size_t)kmax * h * b);
-  w.Yg = c.take<double>((size_t)kmax * h * b);
-  w.Wt = c.take<double>((size_t)n * b);
+  const int64_t pmax = bc_wave_max_groups(n, b), h = 2 * b - 1;
+  w.Vg = c.take<double>((size_t)pmax * h * b);
+  w.Yg = c.take<double>((size_t)pmax * h * b);
+  w.Wt = c.take<double>((size_t)pmax * n * b);
+  w.vg_capacity = (size_t)pmax * h * b;
+  w.wt_capacity = (size_t)pmax * n * b;
   w.gemm_ws = L.gemm_ws;
   w.gemm_ws_bytes = L.gemm_bytes;
   return w;

@@ -14,11 +14,21 @@
 // descending, k ascending, the reflectors of G(J, k) with j descending -- the
 // "bottom to top" group order of Sec. 2.1.2; within a group consecutive
 // reflectors are one row apart, which keeps the rows of X in cache.
+//
+// Wavefronts.  With g = b, G(J, k) touches rows [(J+k) b + 1, (J+k+2) b - 1], so two
+// groups overlap exactly when their diagonal indices D = J + k differ by at most 1.
+// Give G(J, k) the wave number t = k + (nJ - 1 - J).  Every overlapping pair keeps its
+// order: the same J with k ascending raises t, and J1 > J2 with |D1 - D2| <= 1 gives
+// k1 - k2 <= 1 - (J1 - J2) < J1 - J2, i.e. t1 < t2.  Two groups of one wave have
+// D1 - D2 = 2 (J1 - J2), so they are disjoint (2b rows apart) and commute.  Each wave
+// is therefore one batched pair of products: W_p^T = X_p^T V_p and X_p -= Y_p W_p,
+// about 2n/b waves in all instead of n^2/(2 b g) separate groups.
 #include <algorithm>
 #include <cstdio>
 
 #include "device_util.cuh"
 #include "evd_internal.h"
+#include "evd_ozaki.h"
 
 namespace evd {
 
@@ -85,15 +95,16 @@ __global__ void __launch_bounds__(BB_NT) k_bc_back(const double* __restrict__ U,
 // i = j - J g at rows i .. i + b - 1 of the group.  For each group the kernel forms
 // V (h x g, explicit, zero outside the parallelogram), T (g x g upper triangular,
 // H_{j0} ... H_{j0+g-1} = I - V T V^T) and Y = V T.  One CTA per group.
+// Problem p of wave t is the group with J' = jp0 + p, J = nJ - 1 - J', k = t - J'.
 __global__ void __launch_bounds__(256) k_bcback_prep(const double* __restrict__ U, const double* __restrict__ Utau,
-                                                     int64_t n, int b, int g, int64_t J, int64_t kcount, double* Vg,
-                                                     double* Yg, int h) {
+                                                     int64_t n, int b, int g, int64_t nJ, int64_t t, int64_t jp0,
+                                                     double* Vg, double* Yg, int h) {
   extern __shared__ double sp[];
   double* V = sp;                 // V[r + i h], h x g
   double* T = V + (size_t)h * g;  // T[p + i g]
   double* tau = T + (size_t)g * g;
-  const int64_t k = blockIdx.x;
-  if (k >= kcount) return;
+  const int64_t pidx = blockIdx.x;
+  const int64_t J = nJ - 1 - (jp0 + pidx), k = t - (jp0 + pidx);
   const int64_t nsweeps = n - 2;
   for (int idx = threadIdx.x; idx < h * g; idx += blockDim.x) V[idx] = 0.0;
   __syncthreads();
@@ -130,9 +141,9 @@ __global__ void __launch_bounds__(256) k_bcback_prep(const double* __restrict__ 
     }
     __syncthreads();
   }
-  // write V and Y = V T (h x g each, group k at offset k h g)
-  double* Vo = Vg + (size_t)k * h * g;
-  double* Yo = Yg + (size_t)k * h * g;
+  // write V and Y = V T (h x g each, problem p at offset p h g)
+  double* Vo = Vg + (size_t)pidx * h * g;
+  double* Yo = Yg + (size_t)pidx * h * g;
   for (int idx = tid; idx < h * g; idx += 256) {
     const int r = idx % h, i = idx / h;
     double s = 0.0;
@@ -153,6 +164,8 @@ __global__ void k_explicit_v(const double* A, int64_t lda, int64_t r0, int64_t c
 }
 
 }  // namespace
+
+int64_t bc_wave_max_groups(int64_t n, int b) { return (b > 0) ? n / (2 * (int64_t)b) + 2 : 1; }
 
 evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w) {
   const int64_t n = pc.n;
@@ -176,33 +189,49 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
     EVD_CUDA_TRY(cudaFuncSetAttribute(k_bcback_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  for (int64_t J = nJ - 1; J >= 0; --J) {
-    const int64_t kcount = sweep_steps_b(n, b, J * g);  // the block's first sweep has the most steps
-    if (kcount <= 0) continue;
-    {
-      StatScope sc("bc_back_prep", s);
-      k_bcback_prep<<<(unsigned)kcount, dim3(32, 8), smem, s>>>(bw.U, bw.Utau, n, b, g, J, kcount, w.Vg, w.Yg, h); count_launch();
-      EVD_CUDA_TRY(cudaGetLastError());
-    }
-    for (int64_t k = 0; k < kcount; ++k) {
-      const int64_t R0 = J * g + 1 + k * b;
-      const int64_t hh = std::min<int64_t>(h, n - R0);
-      if (hh <= 0) break;
-      const double* V = w.Vg + (size_t)k * h * g;
-      const double* Y = w.Yg + (size_t)k * h * g;
-      // W^T = X(R0:R0+hh, :)^T V   (n x g)
+  auto kc = [&](int64_t J) { return sweep_steps_b(n, b, J * g); };
+  const int64_t tmax = kc(0) + nJ - 2;
+  for (int64_t t = 0; t <= tmax; ++t) {
+    // groups of wave t: J' = nJ - 1 - J in [jlo, jhi] with 0 <= k = t - J' < kc(J)
+    int64_t jp = std::min<int64_t>(t, nJ - 1);
+    while (jp >= 0) {
+      // skip invalid J' (descending), then take the maximal run of valid ones
+      if (t - jp >= kc(nJ - 1 - jp)) { --jp; continue; }
+      const int64_t jhi = jp;
+      while (jp >= 0 && t - jp < kc(nJ - 1 - jp)) --jp;
+      const int64_t jlo = jp + 1;
+      const int count = (int)(jhi - jlo + 1);
+      if ((size_t)count * h * g > w.vg_capacity || (size_t)count * n * g > w.wt_capacity) return EVD_ERR_WORKSPACE;
+      {
+        StatScope sc("bc_back_prep", s);
+        k_bcback_prep<<<(unsigned)count, dim3(32, 8), smem, s>>>(bw.U, bw.Utau, n, b, g, nJ, t, jlo, w.Vg, w.Yg, h); count_launch();
+        EVD_CUDA_TRY(cudaGetLastError());
+      }
+      // problem 0 (J' = jlo) is the lowest group of the run and the only one that may reach row n
+      const int64_t J0 = nJ - 1 - jlo, k0 = t - jlo;
+      const int64_t R0 = J0 * g + 1 + k0 * b;
+      const int64_t hh0 = std::min<int64_t>(h, n - R0);
+      Batch bt;
+      bt.count = count;
+      // W_p^T = X(R0_p : R0_p + h, :)^T V_p   (n x g each), R0_p = R0 - p (g + b)
       Gemm g1;
       g1.status = pc.status;
-      g1.ta = 'T'; g1.m = n; g1.n = g; g1.k = hh; g1.A = Q + R0; g1.lda = ldq; g1.B = V; g1.ldb = h;
+      g1.tag = "bc_back_gemm";
+      g1.ta = 'T'; g1.m = n; g1.n = g; g1.k = h; g1.A = Q + R0; g1.lda = ldq; g1.B = w.Vg; g1.ldb = h;
       g1.C = w.Wt; g1.ldc = n; g1.alpha = 1.0; g1.beta = 0.0;
-      evd_status_t st = gemm(g1, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
+      bt.sA = -(int64_t)(g + b); bt.sB = (int64_t)h * g; bt.sC = n * g; bt.first_k = hh0; bt.first_m = -1;
+      evd_status_t st = (count > 1) ? ozaki_gemm_batched(g1, bt, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s)
+                                    : (g1.k = hh0, gemm(g1, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s));
       if (st != EVD_OK) return st;
-      // X(R0:R0+hh, :) -= Y W
+      // X_p -= Y_p W_p
       Gemm g2;
       g2.status = pc.status;
-      g2.tb = 'T'; g2.m = hh; g2.n = n; g2.k = g; g2.A = Y; g2.lda = h; g2.B = w.Wt; g2.ldb = n;
+      g2.tag = "bc_back_gemm";
+      g2.tb = 'T'; g2.m = h; g2.n = n; g2.k = g; g2.A = w.Yg; g2.lda = h; g2.B = w.Wt; g2.ldb = n;
       g2.C = Q + R0; g2.ldc = ldq; g2.alpha = -1.0; g2.beta = 1.0;
-      st = gemm(g2, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
+      bt.sA = (int64_t)h * g; bt.sB = n * g; bt.sC = -(int64_t)(g + b); bt.first_k = -1; bt.first_m = hh0;
+      st = (count > 1) ? ozaki_gemm_batched(g2, bt, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s)
+                       : (g2.m = hh0, gemm(g2, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s));
       if (st != EVD_OK) return st;
     }
   }

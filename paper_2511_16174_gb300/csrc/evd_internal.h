@@ -124,6 +124,9 @@ struct BcWork {
   unsigned* bar;
 };
 int64_t bc_num_reflectors(int64_t n, int b);
+// Upper bound on the number of reflector groups in one BC-Back wave (groups of a
+// wave start 2b rows apart, all below row n).
+int64_t bc_wave_max_groups(int64_t n, int b);
 evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, bool vectors);
 
 struct DcWork {
@@ -140,9 +143,11 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
 
 struct BackWork {
   double* Tg;      // T factors of the BC reflector groups
-  double* Vg;      // V of the BC reflector groups of one sweep block (kmax x h x g)
+  double* Vg;      // V of the BC reflector groups of one wave (count x h x g)
   double* Yg;      // Y = V T of the same groups
-  double* Wt;      // W^T (n x g)
+  double* Wt;      // W^T of the same groups (count x n x g)
+  size_t vg_capacity = 0;  // doubles available in Vg (and in Yg)
+  size_t wt_capacity = 0;  // doubles available in Wt
   double* Vp;      // explicit V of an SBR panel block (n x nb)
   double* Wp;      // nb x n
   double* Tp;      // nb x nb

@@ -55,6 +55,7 @@ constexpr int OZ_THREADS = 320;
 constexpr int OZ_PERIOD = 16;     // stages between two drains of one weight (256 K-elements)
 constexpr long long OZ_WAIT_LIMIT = 1ll << 26;
 constexpr int OZ_GROUP_M = 8;     // row tiles per rasterization group
+constexpr uint32_t OZ_PARK_BYTES = 256 * 64 * 8;  // epilogue: 2 x 32 int64 sums per epilogue thread
 
 // ------------------------------------------------------------------ operand views
 // Element (rho, kappa) of an operand seen as rows x K:
@@ -65,6 +66,8 @@ struct View {
   int64_t ld;
   int mode;
   int64_t rows, K;
+  int64_t pstride = 0;  // batched: element offset between consecutive problems
+  int64_t K0 = -1;      // batched: K of problem 0 when >= 0 (a truncated first problem)
   __device__ __forceinline__ double get(int64_t r, int64_t k) const {
     if (mode == 0) return p[r + k * ld];
     if (mode == 1) return p[k + r * ld];
@@ -107,8 +110,8 @@ __global__ void k_row_exponent(const View v, int* ex, int64_t kspan) {
   }
 }
 
-// Balanced base-128 digits of T = round_half_away(x 2^(7s - e)).
-__device__ __forceinline__ void ozaki_digits(double x, int e, int s, int* dg) {
+// T = round_half_away(x 2^(7s - e)), the scaled operand as an integer.
+__device__ __forceinline__ long long ozaki_scaled(double x, int e, int s) {
   const long long bits = __double_as_longlong(x);
   int E = (int)((bits >> 52) & 0x7FF);
   long long m = bits & 0xFFFFFFFFFFFFFll;
@@ -123,12 +126,21 @@ __device__ __forceinline__ void ozaki_digits(double x, int e, int s, int* dg) {
     }
     if (bits < 0) T = -T;
   }
-  for (int t = s - 1; t >= 1; --t) {
-    const long long r = ((T + 64) & 127) - 64;
-    dg[t] = (int)r;
-    T = (T - r) >> 7;
-  }
-  dg[0] = (int)T;
+  return T;
+}
+
+// Balanced base-128 digits, each on its own: with the offset
+// O = 64 (1 + 128 + ... + 128^(s-2)), the low s-1 balanced digits of T are the
+// ordinary base-128 digits of T + O minus 64, and the top digit is (T + O) >> 7(s-1).
+// Slice t holds the digit at position s-1-t (slice 0 is the top).
+__device__ __forceinline__ long long ozaki_offset(int s) {
+  long long o = 0;
+  for (int j = 0; j < s - 1; ++j) o = (o << 7) + 64;
+  return o;
+}
+__device__ __forceinline__ int ozaki_digit(long long TO, int s, int t) {
+  const int j = s - 1 - t;
+  return (t == 0) ? (int)(TO >> (7 * j)) : (int)((TO >> (7 * j)) & 127) - 64;
 }
 
 // Slices S[t][rho][kappa] (bfloat16, K-major, rows_pad x K_pad per slice) and the
@@ -147,63 +159,85 @@ __global__ void k_split(const View v, const int* ex_biased, int* ex_frexp, int s
     int eb = (R < v.rows) ? ex_biased[R] : 0;
     const int e = (eb > 0) ? eb - 1022 : -1022;
     if (k0 == 0 && q == 0 && R < rows_pad) ex_frexp[R] = e;
-    int d0[OZ_MAXS], d1[OZ_MAXS];
-    ozaki_digits(t[rr][2 * q], e, s, d0);
-    ozaki_digits(t[rr][2 * q + 1], e, s, d1);
+    const long long off = ozaki_offset(s);
+    const long long T0 = ozaki_scaled(t[rr][2 * q], e, s) + off;
+    const long long T1 = ozaki_scaled(t[rr][2 * q + 1], e, s) + off;
     for (int tt = 0; tt < s; ++tt) {
       __nv_bfloat162 h;
-      h.x = __float2bfloat16_rn((float)d0[tt]);
-      h.y = __float2bfloat16_rn((float)d1[tt]);
+      h.x = __float2bfloat16_rn((float)ozaki_digit(T0, s, tt));
+      h.y = __float2bfloat16_rn((float)ozaki_digit(T1, s, tt));
       *reinterpret_cast<__nv_bfloat162*>(S + ((size_t)tt * rows_pad + R) * K_pad + k0 + 2 * q) = h;
     }
   }
 }
 
-// One-pass variant for short K (K <= 4096): each block owns 32 rows over the whole
-// K range, finds the row exponents, then writes the digits.  Saves the exponent
-// launch and the memset of the two-kernel path.
-__global__ void k_split_fused(const View v, int* ex_frexp, int s, int64_t rows_pad, int64_t K_pad,
-                              __nv_bfloat16* S) {
-  __shared__ double t[32][33];
-  __shared__ int red[8][32];
-  __shared__ int erow[32];
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
-  int mx = 0;
-  for (int64_t k0 = 0; k0 < v.K; k0 += 32) {
-    __syncthreads();
-    load_tile32(v, r0, k0, t);
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += 8) {
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(t[threadIdx.x][k]);
-      mx = max(mx, (int)((bits >> 52) & 0x7FF));
+// One-pass split for short K (K_pad <= 512) of both operands in one launch: block
+// x < nblk_a takes 32 rows of A, the others 32 rows of B.  The block caches its
+// 32 x K_pad rows in shared memory (all loads issued up front), reduces the row
+// exponents, then writes the digits 8 K-elements (16 bytes) per slice at a time.
+__global__ void __launch_bounds__(256) k_split_fused(const View va, int* ea, __nv_bfloat16* SA, int64_t rows_pad_a,
+                                                     const View vb, int* eb, __nv_bfloat16* SB, int64_t rows_pad_b,
+                                                     int nblk_a, int s, int64_t K_pad) {
+  extern __shared__ double tile[];  // [32][K_pad + 1]
+  const bool isA = (int)blockIdx.x < nblk_a;
+  View v = isA ? va : vb;
+  // batched: problem p = blockIdx.y; slices S[t][p rows_pad + r][K_pad], exponents ex[p rows_pad + r]
+  const int64_t pb = blockIdx.y, count = gridDim.y;
+  v.p += pb * v.pstride;
+  if (pb == 0 && v.K0 >= 0) v.K = v.K0;
+  const int64_t rows_pad = isA ? rows_pad_a : rows_pad_b;
+  int* ex = (isA ? ea : eb) + pb * rows_pad;
+  __nv_bfloat16* S = (isA ? SA : SB) + pb * rows_pad * K_pad;
+  const int64_t slice_stride = count * rows_pad * K_pad;
+  const int64_t r0 = (int64_t)(isA ? (int)blockIdx.x : (int)blockIdx.x - nblk_a) * 32;
+  const int ls = (int)K_pad + 1;
+  const int tid = threadIdx.x;
+  const int total = 32 * (int)K_pad;
+  if (v.row_contig()) {
+#pragma unroll 8
+    for (int idx = tid; idx < total; idx += 256) {
+      const int r = idx & 31, k = idx >> 5;
+      const int64_t R = r0 + r;
+      tile[r * ls + k] = (R < v.rows && k < v.K) ? v.get(R, k) : 0.0;
+    }
+  } else {
+#pragma unroll 8
+    for (int idx = tid; idx < total; idx += 256) {
+      const int t2 = idx >> 5;
+      const int r = t2 & 31, k = ((t2 >> 5) << 5) + (idx & 31);
+      const int64_t R = r0 + r;
+      tile[r * ls + k] = (R < v.rows && k < v.K) ? v.get(R, k) : 0.0;
     }
   }
-  red[threadIdx.y][threadIdx.x] = mx;
   __syncthreads();
-  if (threadIdx.y == 0) {
-    for (int y = 1; y < 8; ++y) mx = max(mx, red[y][threadIdx.x]);
-    const int e = (mx > 0) ? mx - 1022 : -1022;
-    erow[threadIdx.x] = e;
-    if (r0 + threadIdx.x < rows_pad) ex_frexp[r0 + threadIdx.x] = e;
-  }
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int q = tid & 15;
-  for (int64_t k0 = 0; k0 < K_pad; k0 += 32) {
-    __syncthreads();
-    load_tile32(v, r0, k0, t);
-    __syncthreads();
-    for (int rr = tid >> 4; rr < 32; rr += 16) {
-      const int64_t R = r0 + rr;
-      const int e = erow[rr];
-      int d0[OZ_MAXS], d1[OZ_MAXS];
-      ozaki_digits(t[rr][2 * q], e, s, d0);
-      ozaki_digits(t[rr][2 * q + 1], e, s, d1);
-      for (int tt = 0; tt < s; ++tt) {
+  // row r = tid / 8: max biased exponent over its K range, 8 threads per row
+  const int r = tid >> 3, q = tid & 7;
+  int mx = 0;
+  for (int k = q; k < (int)K_pad; k += 8)
+    mx = max(mx, (int)((__double_as_longlong(tile[r * ls + k]) >> 52) & 0x7FF));
+  mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+  const int e = (mx > 0) ? mx - 1022 : -1022;
+  const int64_t R = r0 + r;
+  if (q == 0) ex[R] = e;
+  // digits: units of 8 K-elements, unit u = q + 8 j
+  for (int u = q; u < (int)K_pad / 8; u += 8) {
+    const long long off = ozaki_offset(s);
+    long long TO[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) TO[i] = ozaki_scaled(tile[r * ls + 8 * u + i], e, s) + off;
+    for (int tt = 0; tt < s; ++tt) {
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
         __nv_bfloat162 h;
-        h.x = __float2bfloat16_rn((float)d0[tt]);
-        h.y = __float2bfloat16_rn((float)d1[tt]);
-        *reinterpret_cast<__nv_bfloat162*>(S + ((size_t)tt * rows_pad + R) * K_pad + k0 + 2 * q) = h;
+        h.x = __float2bfloat16_rn((float)ozaki_digit(TO[2 * i], s, tt));
+        h.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * i + 1], s, tt));
+        w[i] = *reinterpret_cast<uint32_t*>(&h);
       }
+      *reinterpret_cast<uint4*>(S + (size_t)tt * slice_stride + (size_t)R * K_pad + 8 * u) =
+          make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -303,15 +337,13 @@ __device__ __forceinline__ double i128_to_double(long long hi, unsigned long lon
   } else {
     const int sh = p - 52;  // bits dropped below the 53-bit mantissa
     // m = (mh:ml) >> sh, sticky and round bits
-    unsigned long long q, rem_hi, rem_lo;  // rem = dropped part
+    unsigned long long q;
     if (sh < 64) {
       q = (ml >> sh) | (sh ? (mh << (64 - sh)) : 0ull);
-      rem_lo = sh ? (ml << (64 - sh)) : 0ull;  // dropped bits left-aligned
-      rem_hi = 0ull;
+      const unsigned long long rem_lo = sh ? (ml << (64 - sh)) : 0ull;  // dropped bits, left-aligned
       const unsigned long long half = 1ull << 63;
       const bool round_up = (rem_lo > half) || (rem_lo == half && (q & 1ull));
       m = q + (round_up ? 1ull : 0ull);
-      (void)rem_hi;
     } else {
       const int s2 = sh - 64;
       q = mh >> s2;
@@ -351,6 +383,10 @@ struct MmaArgs {
   int* st;
   int stages_per_split;  // split K: CTA z handles stages [z * stages_per_split, ...)
   double* part;          // split K: partial products (alpha = 1, beta = 0), m x n each, ld m
+  // batched (grid z = problem): problem p reads slice rows p bm_pad + ... of A and
+  // p bn_pad + ... of B and writes C + p sC; problem 0 writes only m_first rows
+  int batched;
+  int64_t bm_pad, bn_pad, sC, m_first;
 };
 
 __device__ __forceinline__ bool drain_after(int j, int nst) {
@@ -373,17 +409,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   if (a.lower && n0 > m0 + OZ_BM - 1) return;  // tile strictly above the diagonal
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int s = a.s, L = s - 1;
-  const int j0 = (int)blockIdx.z * a.stages_per_split;
+  const int64_t pb = a.batched ? (int64_t)blockIdx.z : 0;
+  const int j0 = a.batched ? 0 : (int)blockIdx.z * a.stages_per_split;
   const int nst = (a.nst - j0 < a.stages_per_split) ? a.nst - j0 : a.stages_per_split;
+  const int rowA = (int)(pb * a.bm_pad + m0), rowB = (int)(pb * a.bn_pad + n0);
+  const int* ea = a.ea + pb * a.bm_pad;
+  const int* eb = a.eb + pb * a.bn_pad;
+  double* Cp = a.C + pb * a.sC;
+  const int64_t m_lim = (pb == 0 && a.m_first >= 0) ? a.m_first : a.m;
   const uint32_t a_bytes = (uint32_t)s * OZ_BM * OZ_KS * 2, b_bytes = (uint32_t)s * OZ_BN * OZ_KS * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * stage_bytes);
+  const uint32_t data_bytes = (OZ_STAGES * stage_bytes > OZ_PARK_BYTES) ? OZ_STAGES * stage_bytes : OZ_PARK_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + data_bytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + OZ_STAGES;
   uint64_t* accf = bars + 2 * OZ_STAGES;
   uint64_t* acce = bars + 2 * OZ_STAGES + OZ_MAXS;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 2 * OZ_MAXS);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* eb_s = reinterpret_cast<int*>(tmem_slot + 4);  // column exponents of this tile (OZ_BN ints)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -415,8 +459,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         uint8_t* sa = smem + si * stage_bytes;
         const uint32_t fb = smem_u32(full + si);
         mbar_expect_tx(fb, stage_bytes);
-        tma_load_3d(smem_u32(sa), &tmA, (j0 + j) * OZ_KS, (int)m0, 0, fb);
-        tma_load_3d(smem_u32(sa + a_bytes), &tmB, (j0 + j) * OZ_KS, (int)n0, 0, fb);
+        tma_load_3d(smem_u32(sa), &tmA, (j0 + j) * OZ_KS, rowA, 0, fb);
+        tma_load_3d(smem_u32(sa + a_bytes), &tmB, (j0 + j) * OZ_KS, rowB, 0, fb);
         ++issued;
       }
       if (*abort) {
@@ -467,6 +511,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int quad = warp & 3, half = (warp - 2) >> 2;
     const int64_t row = m0 + quad * 32 + lane;
     const int H = (L < 3) ? L : 3;
+    // exponents first, while the main loop runs: the row's in a register, the
+    // tile's columns in shared memory (named barrier over the 8 epilogue warps)
+    const int etid = threadIdx.x - 64;
+    if (etid < OZ_BN) eb_s[etid] = (n0 + etid < a.n) ? eb[n0 + etid] : 0;
+    const int er = (row < a.m) ? ea[row] : 0;
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     long long Rh[32], Rl[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) { Rh[c] = 0; Rl[c] = 0; }
@@ -479,16 +529,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       tc_fence_after();
       for (int k = 0; k <= L; ++k) {
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + half * 32);
-        const bool hi = (k <= 3);
-        const int sh = hi ? 7 * (H - k) : 7 * (L - k);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float v[16];
           tc_ld16(taddr + 16 * h, v);
-          if (hi) {
+          if (k <= 3) {
+            const int sh = 7 * (H - k);
 #pragma unroll
             for (int c = 0; c < 16; ++c) Rh[16 * h + c] += (long long)__float2int_rn(v[c]) << sh;
           } else {
+            const int sh = 7 * (L - k);
 #pragma unroll
             for (int c = 0; c < 16; ++c) Rl[16 * h + c] += (long long)__float2int_rn(v[c]) << sh;
           }
@@ -498,33 +548,57 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(acce));
     }
-    if (ok && row < a.m) {
-      const int er = a.ea[row];
-      const int shift_hi = 7 * (L - H);  // R = R_hi 2^(7 (L - H)) + R_lo, value R 2^(e_r + f_c - 14 - 7L)
-      const bool alpha_one = (a.alpha == 1.0), alpha_mone = (a.alpha == -1.0);
+    if (ok) {
+      // Every MMA has retired (last accumulator barrier) and every TMA load has
+      // landed, so the stage buffers are idle: park the exact sums there and let a
+      // rolled loop index them.  The output code runs once per CTA, and a fully
+      // unrolled version of it would be fetched cold from L2.
+      long long* park = reinterpret_cast<long long*>(smem) + (threadIdx.x - 64);  // [2 * 32][256]
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        const int64_t col = n0 + half * 32 + c;
-        if (col < a.n && !(a.lower && row < col)) {
-          // exact 128-bit R = Rh << shift_hi + Rl
-          const long long rh = Rh[c];
-          unsigned long long lo = (shift_hi == 0) ? (unsigned long long)rh : ((unsigned long long)rh << shift_hi);
-          long long hi = (shift_hi == 0) ? (rh >> 63) : (rh >> (64 - shift_hi));
-          if (L >= 4) {
-            const long long rl = Rl[c];
-            const unsigned long long nlo = lo + (unsigned long long)rl;
-            hi += (rl >> 63) + (nlo < lo ? 1 : 0);
-            lo = nlo;
+        park[(2 * c) * 256] = Rh[c];
+        park[(2 * c + 1) * 256] = Rl[c];
+      }
+      if (row < m_lim) {
+        const int shift_hi = 7 * (L - H);  // R = R_hi 2^(7 (L - H)) + R_lo, value R 2^(e_r + f_c - 14 - 7L)
+        const bool alpha_one = (a.alpha == 1.0), alpha_mone = (a.alpha == -1.0);
+        const bool read_c = (a.part == nullptr) && (a.beta != 0.0);
+        double* crow = Cp + row;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 32; c0 += 4) {
+          // the 4 loads of C go out before any store so that they overlap
+          double cv[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int64_t col = n0 + half * 32 + c0 + c;
+            const bool valid = col < a.n && !(a.lower && row < col);
+            cv[c] = (read_c && valid) ? crow[col * a.ldc] : 0.0;
           }
-          double v = i128_to_double(hi, lo, er + a.eb[col] - 14 - 7 * L);
-          if (a.part) {
-            a.part[(size_t)blockIdx.z * a.m * a.n + row + col * a.m] = v;
-          } else {
-            if (alpha_mone) v = -v;
-            else if (!alpha_one) v *= a.alpha;
-            double* p = a.C + row + col * a.ldc;
-            if (a.beta != 0.0) v = (a.beta == 1.0) ? (*p + v) : fma(a.beta, *p, v);
-            *p = v;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int cc = c0 + c;
+            const int64_t col = n0 + half * 32 + cc;
+            if (col < a.n && !(a.lower && row < col)) {
+              // exact 128-bit R = Rh << shift_hi + Rl
+              const long long rh = park[(2 * cc) * 256];
+              unsigned long long lo = (shift_hi == 0) ? (unsigned long long)rh : ((unsigned long long)rh << shift_hi);
+              long long hi = (shift_hi == 0) ? (rh >> 63) : (rh >> (64 - shift_hi));
+              if (L >= 4) {
+                const long long rl = park[(2 * cc + 1) * 256];
+                const unsigned long long nlo = lo + (unsigned long long)rl;
+                hi += (rl >> 63) + (nlo < lo ? 1 : 0);
+                lo = nlo;
+              }
+              double v = i128_to_double(hi, lo, er + eb_s[half * 32 + cc] - 14 - 7 * L);
+              if (a.part) {
+                a.part[(size_t)blockIdx.z * a.m * a.n + row + col * a.m] = v;
+              } else {
+                if (alpha_mone) v = -v;
+                else if (!alpha_one) v *= a.alpha;
+                if (read_c) v = (a.beta == 1.0) ? (cv[c] + v) : fma(a.beta, cv[c], v);
+                crow[col * a.ldc] = v;
+              }
+            }
           }
         }
       }
@@ -633,23 +707,28 @@ size_t splitk_bytes(int64_t m, int64_t n, int64_t k) {
 }
 
 size_t smem_bytes(int s) {
-  return 1024 + (size_t)OZ_STAGES * s * (OZ_BM + OZ_BN) * OZ_KS * 2 + (2 * OZ_STAGES + 2 * OZ_MAXS) * 8 + 16;
+  const size_t stages = (size_t)OZ_STAGES * s * (OZ_BM + OZ_BN) * OZ_KS * 2;
+  return 1024 + std::max<size_t>(stages, OZ_PARK_BYTES) + (2 * OZ_STAGES + 2 * OZ_MAXS) * 8 + 16 + OZ_BN * 4;
 }
 
 }  // namespace
 
-size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
-  if (slices <= 0) return 0;
+size_t ozaki_scratch_bytes_batched(int64_t m, int64_t n, int64_t k, int slices, int count) {
+  if (slices <= 0 || count <= 0) return 0;
   Pads p = pads(m, n, k);
   Carver c(nullptr);
-  c.take<__nv_bfloat16>((size_t)slices * p.m_pad * p.k_pad);
-  c.take<__nv_bfloat16>((size_t)slices * p.n_pad * p.k_pad);
+  c.take<__nv_bfloat16>((size_t)slices * count * p.m_pad * p.k_pad);
+  c.take<__nv_bfloat16>((size_t)slices * count * p.n_pad * p.k_pad);
   c.take<int>((size_t)p.m_pad);
   c.take<int>((size_t)p.n_pad);
-  c.take<int>((size_t)p.m_pad);
-  c.take<int>((size_t)p.n_pad);
-  c.take<double>(splitk_bytes(m, n, k) / sizeof(double));
+  c.take<int>((size_t)count * p.m_pad);
+  c.take<int>((size_t)count * p.n_pad);
+  c.take<double>(count == 1 ? splitk_bytes(m, n, k) / sizeof(double) : 0);
   return c.off + 256;
+}
+
+size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
+  return ozaki_scratch_bytes_batched(m, n, k, slices, 1);
 }
 
 bool ozaki_eligible(const Gemm& g) {
@@ -658,33 +737,49 @@ bool ozaki_eligible(const Gemm& g) {
   return 2.0 * (double)g.m * (double)g.n * (double)g.k >= 6.7e7;
 }
 
-evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes, cudaStream_t s) {
+evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void* scratch, size_t scratch_bytes,
+                                cudaStream_t s) {
   if (slices < 1 || slices > OZ_MAXS) return EVD_ERR_INVALID_ARG;
-  if (scratch_bytes < ozaki_scratch_bytes(g.m, g.n, g.k, slices) || !scratch) return EVD_ERR_WORKSPACE;
+  const int count = bt.count;
+  if (count < 1 || count > 65535) return EVD_ERR_INVALID_ARG;
+  if (count > 1 && (g.lower || g.a_sym_lower)) return EVD_ERR_INVALID_ARG;
+  if (scratch_bytes < ozaki_scratch_bytes_batched(g.m, g.n, g.k, slices, count) || !scratch) return EVD_ERR_WORKSPACE;
   if (g.k > ((int64_t)1 << 17)) return EVD_ERR_NOT_SUPPORTED;  // exactness bound of the int64 sums
   const Pads p = pads(g.m, g.n, g.k);
+  if (count > 1 && p.k_pad > 512) return EVD_ERR_NOT_SUPPORTED;  // batched products use the one-pass split
+  if ((int64_t)count * std::max(p.m_pad, p.n_pad) > ((int64_t)1 << 31) - 1) return EVD_ERR_NOT_SUPPORTED;
   Carver c(scratch);
-  __nv_bfloat16* SA = c.take<__nv_bfloat16>((size_t)slices * p.m_pad * p.k_pad);
-  __nv_bfloat16* SB = c.take<__nv_bfloat16>((size_t)slices * p.n_pad * p.k_pad);
+  __nv_bfloat16* SA = c.take<__nv_bfloat16>((size_t)slices * count * p.m_pad * p.k_pad);
+  __nv_bfloat16* SB = c.take<__nv_bfloat16>((size_t)slices * count * p.n_pad * p.k_pad);
   int* exA = c.take<int>((size_t)p.m_pad);
   int* exB = c.take<int>((size_t)p.n_pad);
-  int* eA = c.take<int>((size_t)p.m_pad);
-  int* eB = c.take<int>((size_t)p.n_pad);
-  const int splits = splitk_count(g.m, g.n, g.k);
-  double* part = c.take<double>(splitk_bytes(g.m, g.n, g.k) / sizeof(double));
+  int* eA = c.take<int>((size_t)count * p.m_pad);
+  int* eB = c.take<int>((size_t)count * p.n_pad);
+  const int splits = (count == 1) ? splitk_count(g.m, g.n, g.k) : 1;
+  double* part = c.take<double>(count == 1 ? splitk_bytes(g.m, g.n, g.k) / sizeof(double) : 0);
   View va, vb;
   va.p = g.A; va.ld = g.lda; va.rows = g.m; va.K = g.k;
   va.mode = g.a_sym_lower ? 2 : (g.ta == 'N' ? 0 : 1);
+  va.pstride = bt.sA; va.K0 = (count > 1 && bt.first_k >= 0) ? std::min<int64_t>(bt.first_k, g.k) : -1;
   vb.p = g.B; vb.ld = g.ldb; vb.rows = g.n; vb.K = g.k;
   vb.mode = (g.tb == 'N') ? 1 : 0;
-  const double flops = (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;
+  vb.pstride = bt.sB;
+  const double flops = (double)count * (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;
   {
-    StatScope sc("gemm_tc_split_prep", s, 0.0,
-                 8.0 * (double)(g.m + g.n) * (double)g.k * 2.0 + 2.0 * slices * (double)(p.m_pad + p.n_pad) * p.k_pad);
+    StatScope sc(g.tag ? "gemm_tc_split_prep_tagged" : "gemm_tc_split_prep", s, 0.0,
+                 (double)count * (8.0 * (double)(g.m + g.n) * (double)g.k * 2.0 +
+                                  2.0 * slices * (double)(p.m_pad + p.n_pad) * p.k_pad));
     dim3 blk(32, 8);
     if (p.k_pad <= 512) {
-      k_split_fused<<<(unsigned)(p.m_pad / 32), blk, 0, s>>>(va, eA, slices, p.m_pad, p.k_pad, SA); count_launch();
-      k_split_fused<<<(unsigned)(p.n_pad / 32), blk, 0, s>>>(vb, eB, slices, p.n_pad, p.k_pad, SB); count_launch();
+      static bool fused_attr = false;
+      if (!fused_attr) {
+        EVD_CUDA_TRY(cudaFuncSetAttribute(k_split_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(32 * (512 + 1) * sizeof(double))));
+        fused_attr = true;
+      }
+      const int nblk_a = (int)(p.m_pad / 32), nblk_b = (int)(p.n_pad / 32);
+      k_split_fused<<<dim3((unsigned)(nblk_a + nblk_b), (unsigned)count), 256, 32 * (p.k_pad + 1) * sizeof(double),
+                      s>>>(va, eA, SA, p.m_pad, vb, eB, SB, p.n_pad, nblk_a, slices, p.k_pad); count_launch();
     } else {
       EVD_CUDA_TRY(cudaMemsetAsync(exA, 0, sizeof(int) * p.m_pad, s));
       EVD_CUDA_TRY(cudaMemsetAsync(exB, 0, sizeof(int) * p.n_pad, s));
@@ -699,7 +794,8 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
     EVD_CUDA_TRY(cudaGetLastError());
   }
   CUtensorMap tmA, tmB;
-  if (!make_map(&tmA, SA, p.k_pad, p.m_pad, slices, OZ_BM) || !make_map(&tmB, SB, p.k_pad, p.n_pad, slices, OZ_BN))
+  if (!make_map(&tmA, SA, p.k_pad, count * p.m_pad, slices, OZ_BM) ||
+      !make_map(&tmB, SB, p.k_pad, count * p.n_pad, slices, OZ_BN))
     return EVD_ERR_CUDA;
   MmaArgs a;
   a.m = g.m; a.n = g.n; a.s = slices; a.nst = (int)(p.k_pad / OZ_KS);
@@ -708,6 +804,9 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
   a.tmem_cols = cols;
   a.ea = eA; a.eb = eB; a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha; a.beta = g.beta;
   a.lower = g.lower ? 1 : 0; a.st = nullptr;
+  a.batched = (count > 1) ? 1 : 0;
+  a.bm_pad = p.m_pad; a.bn_pad = p.n_pad; a.sC = bt.sC;
+  a.m_first = (count > 1 && bt.first_m >= 0) ? std::min<int64_t>(bt.first_m, g.m) : -1;
   {
     // stages per split: a multiple of the drain period so chunks stay aligned
     const int per = (int)ceil_div(ceil_div(a.nst, splits), OZ_PERIOD) * OZ_PERIOD;
@@ -716,7 +815,7 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
   const int zsplits = (int)ceil_div(a.nst, a.stages_per_split);
   a.part = (zsplits > 1) ? part : nullptr;
   static int* d_dummy_status = nullptr;  // status word for timeouts of standalone products
-  if (!d_dummy_status) {
+  if (!g.status && !d_dummy_status) {
     if (cudaMalloc(&d_dummy_status, sizeof(int) * kStatusWords) != cudaSuccess) return EVD_ERR_OOM;
     cudaMemset(d_dummy_status, 0, sizeof(int) * kStatusWords);
   }
@@ -728,7 +827,7 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
                                       (int)smem_bytes(OZ_MAXS)));
     attr_set = true;
   }
-  dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)zsplits);
+  dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)(count > 1 ? count : zsplits));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
   StatScope sc(g.tag ? g.tag : "gemm_tc_split", s, flops * (double)(slices * (slices + 1) / 2));
   k_ozaki_mma<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, a); count_launch();
@@ -742,6 +841,10 @@ evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch
     EVD_CUDA_TRY(cudaGetLastError());
   }
   return EVD_OK;
+}
+
+evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes, cudaStream_t s) {
+  return ozaki_gemm_batched(g, Batch(), slices, scratch, scratch_bytes, s);
 }
 
 }  // namespace evd

@@ -18,6 +18,7 @@
 // of sweep j-1 touch disjoint entries, and every entry sweep j reads has already
 // received all of sweep j-1's updates that precede it in sweep order.
 #include <climits>
+#include <cstdlib>
 #include <cstdio>
 
 #include "device_util.cuh"
@@ -326,6 +327,177 @@ __global__ void __launch_bounds__(BC_NT) k_bulge_chase_smem(const BcArgs a) {
   }
 }
 
+// Carried form (b <= BM, NT = 4 BM threads).  Differences from the step above:
+//  * the block below written by step k, A(R_{k+1}, R_k), is exactly the left block
+//    A(R_{k+1}, c' : r0'-1) of step k+1 (c' = r0 = r0' - b), and no other sweep
+//    touches it in between (sweep j-1 is >= 3 steps ahead, sweep j+1 >= 3 behind),
+//    so it stays in shared memory: the two buffers swap roles, the block is
+//    written back once, as the left block of step k+1 (or at the sweep's end);
+//  * the symmetric mat-vec reads the lower triangle of the diagonal block only;
+//  * alpha = tau w^T v / 2 is formed redundantly by every warp (no extra barrier).
+// Per step: one wait, five block barriers.  Same reflectors, same arithmetic per
+// entry as the other forms up to the order of the dot-product partial sums.
+template <int BM>
+__global__ void __launch_bounds__(4 * BM) k_bulge_chase_carry(const BcArgs a) {
+  constexpr int NT = 4 * BM, TPR = 4, LD = BM + 1;
+  extern __shared__ double smb[];
+  double* Ds = smb;                 // Ds[q * LD + p] = A(r0 + p, r0 + q), p >= q
+  double* buf0 = Ds + BM * LD;      // left block  L[cc * LD + t] = A(r0 + t, c + cc)
+  double* buf1 = buf0 + BM * LD;    // block below B[t * LD + rr] = A(r1 + 1 + rr, r0 + t)
+  __shared__ double v[BM], wv[BM];
+  __shared__ double par[4];
+  const int b = a.b, ldb = 2 * b + 1;
+  const int64_t n = a.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = tid / TPR, sub = tid % TPR;
+  for (int64_t j = blockIdx.x; j + 3 <= n; j += gridDim.x) {
+    const int64_t K = sweep_steps(n, b, j);
+    const int64_t Kprev = (j > 0) ? sweep_steps(n, b, j - 1) : 0;
+    const int64_t uoff = sweep_offset(n, b, j);
+    double* Ls = buf0;
+    double* Bs = buf1;
+    for (int64_t k = 0; k < K; ++k) {
+      if (j > 0) {
+        int64_t need = k + BC_LAG;
+        if (need > Kprev) need = Kprev;
+        if (tid == 0) par[3] = wait_geq(a.prog + (j - 1), (int)need, a.st, (int)(j + 1)) ? 0.0 : 1.0;
+        __syncthreads();
+        if (par[3] != 0.0) return;
+      }
+      const int64_t r0 = j + 1 + k * b;
+      const int64_t r1 = (r0 + b - 1 < n - 1) ? r0 + b - 1 : n - 1;
+      const int m = (int)(r1 - r0 + 1);
+      const int64_t c = (k == 0) ? j : r0 - b;
+      const int ncol = (int)(r0 - c);                                   // 1 for k = 0, b otherwise
+      const int mb = (int)(((r1 + b < n - 1) ? r1 + b : n - 1) - r1);   // rows of the block below
+      // ---- loads: diagonal block (lower), block below, and the left column at k = 0
+#pragma unroll
+      for (int it = 0; it < BM * BM / NT; ++it) {
+        const int idx = tid + it * NT;
+        const int p = idx % BM, q = idx / BM;
+        if (p < m && q <= p) Ds[q * LD + p] = bget(a.band, ldb, r0 + p, r0 + q);
+        if (p < mb && q < m) Bs[q * LD + p] = bget(a.band, ldb, r1 + 1 + p, r0 + q);
+      }
+      if (k == 0 && tid < m) Ls[tid] = bget(a.band, ldb, r0 + tid, c);
+      __syncthreads();
+      // ---- reflector from x = L(:, 0), by warp 0; v into shared memory
+      if (warp == 0) {
+        double ss = 0.0;
+        for (int t = 1 + lane; t < m; t += 32) { const double x = Ls[t]; ss += x * x; }
+        ss = warp_sum(ss);
+        const double alpha = Ls[0];
+        double tau = 0.0, beta = alpha, scale = 0.0;
+        if (ss != 0.0) {
+          const double nrm = sqrt(alpha * alpha + ss);
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        for (int t = lane; t < BM; t += 32) {
+          v[t] = (t == 0) ? 1.0 : (t < m ? Ls[t] * scale : 0.0);
+          if (t < m) Ls[t] = (t == 0) ? beta : 0.0;
+        }
+        if (lane == 0) par[0] = tau;
+      }
+      __syncthreads();
+      const double tau = par[0];
+      if (a.U) {
+        const int64_t idx = uoff + k;
+        if (tid < b) a.U[idx * b + tid] = v[tid];
+        if (tid == 0) a.Utau[idx] = tau;
+      }
+      if (tau != 0.0) {
+        // left application to the rest of the bulge: column cc = 1 + grp of L
+        {
+          const int cc = 1 + grp;
+          double d0 = 0.0, d1 = 0.0;
+          if (cc < ncol) {
+            int t = sub;
+            for (; t + TPR < m; t += 2 * TPR) { d0 += v[t] * Ls[cc * LD + t]; d1 += v[t + TPR] * Ls[cc * LD + t + TPR]; }
+            if (t < m) d0 += v[t] * Ls[cc * LD + t];
+          }
+          double dot = d0 + d1;  // the shuffles run on every lane (converged warp)
+          dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+          dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+          if (cc < ncol) {
+            dot *= tau;
+            for (int t2 = sub; t2 < m; t2 += TPR) Ls[cc * LD + t2] -= dot * v[t2];
+          }
+        }
+        // w = tau D v from the lower triangle: row p = grp
+        {
+          const int p = grp;
+          double d0 = 0.0;
+          if (p < m) {
+            for (int q = sub; q < m; q += TPR) d0 += ((q <= p) ? Ds[q * LD + p] : Ds[p * LD + q]) * v[q];
+          }
+          d0 += __shfl_xor_sync(0xffffffffu, d0, 1);
+          d0 += __shfl_xor_sync(0xffffffffu, d0, 2);
+          if (p < m && sub == 0) wv[p] = tau * d0;
+        }
+        // right application to the block below: row rr = grp
+        {
+          const int rr = grp;
+          double d0 = 0.0, d1 = 0.0;
+          if (rr < mb) {
+            int t = sub;
+            for (; t + TPR < m; t += 2 * TPR) { d0 += Bs[t * LD + rr] * v[t]; d1 += Bs[(t + TPR) * LD + rr] * v[t + TPR]; }
+            if (t < m) d0 += Bs[t * LD + rr] * v[t];
+          }
+          double dot = d0 + d1;
+          dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+          dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+          if (rr < mb) {
+            dot *= tau;
+            for (int t = sub; t < m; t += TPR) Bs[t * LD + rr] -= dot * v[t];
+          }
+        }
+        __syncthreads();
+        // alpha = tau w^T v / 2, formed by every warp
+        double pv = 0.0;
+        for (int t = lane; t < m; t += 32) pv += wv[t] * v[t];
+        pv = warp_sum(pv);
+        const double alpha = 0.5 * tau * pv;
+        // rank-2 update of the lower triangle with w - alpha v
+#pragma unroll
+        for (int it = 0; it < BM * BM / NT; ++it) {
+          const int idx = tid + it * NT;
+          const int p = idx % BM, q = idx / BM;
+          if (p < m && q <= p) {
+            const double wp = wv[p] - alpha * v[p], wq = wv[q] - alpha * v[q];
+            Ds[q * LD + p] -= v[p] * wq + wp * v[q];
+          }
+        }
+      }
+      __syncthreads();
+      // ---- write back the diagonal block and the left block; the block below
+      // becomes the next step's left block (written back at the sweep's end)
+#pragma unroll
+      for (int it = 0; it < BM * BM / NT; ++it) {
+        const int idx = tid + it * NT;
+        const int p = idx % BM, q = idx / BM;
+        if (p < m && q <= p) bput(a.band, ldb, r0 + p, r0 + q, Ds[q * LD + p]);
+        if (p < m && q < ncol) bput(a.band, ldb, r0 + p, c + q, Ls[q * LD + p]);
+      }
+      if (k + 1 == K) {
+#pragma unroll
+        for (int it = 0; it < BM * BM / NT; ++it) {
+          const int idx = tid + it * NT;
+          const int p = idx % BM, q = idx / BM;
+          if (p < mb && q < m) bput(a.band, ldb, r1 + 1 + p, r0 + q, Bs[q * LD + p]);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(a.prog + j, (int)(k + 1));
+      }
+      double* tmp = Ls; Ls = Bs; Bs = tmp;
+    }
+    if (K == 0 && tid == 0) st_release(a.prog + j, 0);
+  }
+}
+
 __global__ void k_extract_tridiag(const double* band, int b, int64_t n, double* d, double* e) {
   const int ldb = 2 * b + 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -353,22 +525,29 @@ evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, b
     a.prog = w.prog; a.st = pc.status;
     const void* kern = (const void*)k_bulge_chase;
     size_t smem = 0;
-    if (pc.b <= 32) {
-      kern = (const void*)k_bulge_chase_smem<32>;
+    int nt = BC_NT;
+    static const int variant = [] {
+      const char* e = getenv("EVD_BC_KERNEL");  // 0: global, 1: staged, 2: carried (default)
+      return e ? atoi(e) : 2;
+    }();
+    if (variant >= 1 && pc.b <= 32) {
+      kern = (variant == 2) ? (const void*)k_bulge_chase_carry<32> : (const void*)k_bulge_chase_smem<32>;
       smem = 3 * 32 * 33 * sizeof(double);
-    } else if (pc.b <= 64) {
-      kern = (const void*)k_bulge_chase_smem<64>;
+      nt = (variant == 2) ? 128 : BC_NT;
+    } else if (variant >= 1 && pc.b <= 64) {
+      kern = (variant == 2) ? (const void*)k_bulge_chase_carry<64> : (const void*)k_bulge_chase_smem<64>;
       smem = 3 * 64 * 65 * sizeof(double);
+      nt = (variant == 2) ? 256 : BC_NT;
     }
     if (smem > 48 * 1024) EVD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int maxG = max_coresident_blocks(kern, BC_NT, smem);
+    int maxG = max_coresident_blocks(kern, nt, smem);
     int64_t G = n - 2;
     if (G > maxG) G = maxG;
     void* args[] = {&a};
     // model bytes (each step reads and writes its 2b x b window; U written once)
     const double nn = (double)n * (double)n;
     StatScope sc("bc_chase", s, 5.0 * pc.b * nn, 16.0 * pc.b * nn + (vectors ? 4.0 * nn : 0.0));
-    EVD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(BC_NT), args, smem, s)); count_launch();
+    EVD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(nt), args, smem, s)); count_launch();
   }
   if (n > 0) {
     k_extract_tridiag<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(w.band, pc.b, n, d, e); count_launch();

@@ -30,6 +30,7 @@ namespace {
 
 constexpr int BC_NT = 128;
 constexpr int BC_LAG = 3;  // sweep j step k waits for sweep j-1 to finish step k + BC_LAG - 1
+constexpr int BC_LAG_CARRY = 2;  // the look-ahead form publishes beta one step early
 
 // Number of steps of sweep j: steps with |R_k| >= 2.
 __host__ __device__ inline int64_t sweep_steps(int64_t n, int b, int64_t j) {
@@ -327,16 +328,26 @@ __global__ void __launch_bounds__(BC_NT) k_bulge_chase_smem(const BcArgs a) {
   }
 }
 
-// Carried form (b <= BM, NT = 4 BM threads).  Differences from the step above:
-//  * the block below written by step k, A(R_{k+1}, R_k), is exactly the left block
+// Carried, look-ahead form (b <= BM, NT = 4 BM threads).
+//  * The block below written by step k, A(R_{k+1}, R_k), is exactly the left block
 //    A(R_{k+1}, c' : r0'-1) of step k+1 (c' = r0 = r0' - b), and no other sweep
-//    touches it in between (sweep j-1 is >= 3 steps ahead, sweep j+1 >= 3 behind),
-//    so it stays in shared memory: the two buffers swap roles, the block is
-//    written back once, as the left block of step k+1 (or at the sweep's end);
-//  * the symmetric mat-vec reads the lower triangle of the diagonal block only;
-//  * alpha = tau w^T v / 2 is formed redundantly by every warp (no extra barrier).
-// Per step: one wait, five block barriers.  Same reflectors, same arithmetic per
-// entry as the other forms up to the order of the dot-product partial sums.
+//    touches it in between, so it stays in shared memory: the two buffers swap
+//    roles and the block is written back once, as step k+1's left block (or at the
+//    sweep's end).
+//  * Its first column is final once step k has applied its reflector from the
+//    right, so warp 0 forms step k+1's reflector then, while the other warps finish
+//    step k (the FP64 square root and divisions leave the critical path), and
+//    stores step k+1's beta -- A(r0', c') -- to the band at once.
+//  * Lag 2.  Sweep j step k touches the entries of sweep j-1 step k+2 only at that
+//    step's beta entry (sweep j's block below reaches row r1 + b = r0' of sweep
+//    j-1, column r1 = c').  Since beta is published within sweep j-1's step k+1,
+//    sweep j step k may start as soon as sweep j-1 has completed step k+1; the
+//    later write-back of the left block of step k+2 skips that entry, which sweep
+//    j may already have updated.
+//  * The symmetric mat-vec reads the lower triangle only; alpha = tau w^T v / 2
+//    is formed by every warp, and w - alpha v once per entry.
+// Same reflectors, same arithmetic per entry as the other forms up to the order
+// of the dot-product partial sums.
 template <int BM>
 __global__ void __launch_bounds__(4 * BM) k_bulge_chase_carry(const BcArgs a) {
   constexpr int NT = 4 * BM, TPR = 4, LD = BM + 1;
@@ -344,8 +355,8 @@ __global__ void __launch_bounds__(4 * BM) k_bulge_chase_carry(const BcArgs a) {
   double* Ds = smb;                 // Ds[q * LD + p] = A(r0 + p, r0 + q), p >= q
   double* buf0 = Ds + BM * LD;      // left block  L[cc * LD + t] = A(r0 + t, c + cc)
   double* buf1 = buf0 + BM * LD;    // block below B[t * LD + rr] = A(r1 + 1 + rr, r0 + t)
-  __shared__ double v[BM], wv[BM];
-  __shared__ double par[4];
+  __shared__ double vb0[BM], vb1[BM], wv[BM];
+  __shared__ double par[4];         // [0] tau of this step, [1] tau of the next, [3] abort
   const int b = a.b, ldb = 2 * b + 1;
   const int64_t n = a.n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -356,9 +367,11 @@ __global__ void __launch_bounds__(4 * BM) k_bulge_chase_carry(const BcArgs a) {
     const int64_t uoff = sweep_offset(n, b, j);
     double* Ls = buf0;
     double* Bs = buf1;
+    double* v = vb0;
+    double* vn = vb1;
     for (int64_t k = 0; k < K; ++k) {
       if (j > 0) {
-        int64_t need = k + BC_LAG;
+        int64_t need = k + BC_LAG_CARRY;
         if (need > Kprev) need = Kprev;
         if (tid == 0) par[3] = wait_geq(a.prog + (j - 1), (int)need, a.st, (int)(j + 1)) ? 0.0 : 1.0;
         __syncthreads();
@@ -380,32 +393,33 @@ __global__ void __launch_bounds__(4 * BM) k_bulge_chase_carry(const BcArgs a) {
       }
       if (k == 0 && tid < m) Ls[tid] = bget(a.band, ldb, r0 + tid, c);
       __syncthreads();
-      // ---- reflector from x = L(:, 0), by warp 0; v into shared memory
-      if (warp == 0) {
-        double ss = 0.0;
-        for (int t = 1 + lane; t < m; t += 32) { const double x = Ls[t]; ss += x * x; }
-        ss = warp_sum(ss);
-        const double alpha = Ls[0];
-        double tau = 0.0, beta = alpha, scale = 0.0;
-        if (ss != 0.0) {
-          const double nrm = sqrt(alpha * alpha + ss);
-          beta = (alpha >= 0.0) ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-          scale = 1.0 / (alpha - beta);
+      if (k == 0) {
+        // ---- the first reflector of the sweep, from x = L(:, 0), by warp 0
+        if (warp == 0) {
+          double ss = 0.0;
+          for (int t = 1 + lane; t < m; t += 32) { const double x = Ls[t]; ss += x * x; }
+          ss = warp_sum(ss);
+          const double alpha = Ls[0];
+          double tau = 0.0, beta = alpha, scale = 0.0;
+          if (ss != 0.0) {
+            const double nrm = sqrt(alpha * alpha + ss);
+            beta = (alpha >= 0.0) ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+          }
+          for (int t = lane; t < BM; t += 32) {
+            v[t] = (t == 0) ? 1.0 : (t < m ? Ls[t] * scale : 0.0);
+            if (t < m) Ls[t] = (t == 0) ? beta : 0.0;
+          }
+          if (lane == 0) par[0] = tau;
+          if (a.U) {
+            for (int t = lane; t < b; t += 32) a.U[uoff * b + t] = v[t];
+            if (lane == 0) a.Utau[uoff] = tau;
+          }
         }
-        for (int t = lane; t < BM; t += 32) {
-          v[t] = (t == 0) ? 1.0 : (t < m ? Ls[t] * scale : 0.0);
-          if (t < m) Ls[t] = (t == 0) ? beta : 0.0;
-        }
-        if (lane == 0) par[0] = tau;
+        __syncthreads();
       }
-      __syncthreads();
       const double tau = par[0];
-      if (a.U) {
-        const int64_t idx = uoff + k;
-        if (tid < b) a.U[idx * b + tid] = v[tid];
-        if (tid == 0) a.Utau[idx] = tau;
-      }
       if (tau != 0.0) {
         // left application to the rest of the bulge: column cc = 1 + grp of L
         {
@@ -452,34 +466,66 @@ __global__ void __launch_bounds__(4 * BM) k_bulge_chase_carry(const BcArgs a) {
             for (int t = sub; t < m; t += TPR) Bs[t * LD + rr] -= dot * v[t];
           }
         }
-        __syncthreads();
-        // alpha = tau w^T v / 2, formed by every warp
+      }
+      __syncthreads();
+      const bool next = (k + 1 < K);
+      if (warp == 0 && next) {
+        // ---- look-ahead: step k+1's reflector from the final first column of the
+        // block below; publish its beta entry now
+        const int m1 = mb;
+        double ss = 0.0;
+        for (int t = 1 + lane; t < m1; t += 32) { const double x = Bs[t]; ss += x * x; }
+        ss = warp_sum(ss);
+        const double alpha = Bs[0];
+        double tau1 = 0.0, beta = alpha, scale = 0.0;
+        if (ss != 0.0) {
+          const double nrm = sqrt(alpha * alpha + ss);
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau1 = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        for (int t = lane; t < BM; t += 32) {
+          vn[t] = (t == 0) ? 1.0 : (t < m1 ? Bs[t] * scale : 0.0);
+          if (t < m1) Bs[t] = (t == 0) ? beta : 0.0;
+        }
+        if (lane == 0) {
+          par[1] = tau1;
+          bput(a.band, ldb, r1 + 1, r0, beta);
+        }
+        if (a.U) {
+          for (int t = lane; t < b; t += 32) a.U[(uoff + k + 1) * b + t] = vn[t];
+          if (lane == 0) a.Utau[uoff + k + 1] = tau1;
+        }
+      }
+      if (tau != 0.0) {
+        // w <- w - alpha v (alpha = tau w^T v / 2, formed by every warp), then the
+        // rank-2 update of the lower triangle
         double pv = 0.0;
         for (int t = lane; t < m; t += 32) pv += wv[t] * v[t];
         pv = warp_sum(pv);
         const double alpha = 0.5 * tau * pv;
-        // rank-2 update of the lower triangle with w - alpha v
+        __syncthreads();  // (every warp has read wv)
+        if (tid < m) wv[tid] -= alpha * v[tid];
+        __syncthreads();
 #pragma unroll
         for (int it = 0; it < BM * BM / NT; ++it) {
           const int idx = tid + it * NT;
           const int p = idx % BM, q = idx / BM;
-          if (p < m && q <= p) {
-            const double wp = wv[p] - alpha * v[p], wq = wv[q] - alpha * v[q];
-            Ds[q * LD + p] -= v[p] * wq + wp * v[q];
-          }
+          if (p < m && q <= p) Ds[q * LD + p] -= v[p] * wv[q] + wv[p] * v[q];
         }
       }
       __syncthreads();
-      // ---- write back the diagonal block and the left block; the block below
-      // becomes the next step's left block (written back at the sweep's end)
+      // ---- write back the diagonal block and the left block (its beta entry was
+      // published one step earlier, for k >= 1); the block below becomes the next
+      // step's left block, or is written back at the sweep's end
 #pragma unroll
       for (int it = 0; it < BM * BM / NT; ++it) {
         const int idx = tid + it * NT;
         const int p = idx % BM, q = idx / BM;
         if (p < m && q <= p) bput(a.band, ldb, r0 + p, r0 + q, Ds[q * LD + p]);
-        if (p < m && q < ncol) bput(a.band, ldb, r0 + p, c + q, Ls[q * LD + p]);
+        if (p < m && q < ncol && (k == 0 || p != 0 || q != 0)) bput(a.band, ldb, r0 + p, c + q, Ls[q * LD + p]);
       }
-      if (k + 1 == K) {
+      if (!next) {
 #pragma unroll
         for (int it = 0; it < BM * BM / NT; ++it) {
           const int idx = tid + it * NT;
@@ -491,8 +537,10 @@ __global__ void __launch_bounds__(4 * BM) k_bulge_chase_carry(const BcArgs a) {
       if (tid == 0) {
         __threadfence();
         st_release(a.prog + j, (int)(k + 1));
+        par[0] = par[1];
       }
       double* tmp = Ls; Ls = Bs; Bs = tmp;
+      tmp = v; v = vn; vn = tmp;
     }
     if (K == 0 && tid == 0) st_release(a.prog + j, 0);
   }

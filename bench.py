@@ -34,7 +34,7 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "n=49152 EVD seconds & effective TFLOPS; split-precision vs FP64 at equal residual"
 DEFAULT_N = 8192
-FP64_ALU_PEAK_TFLOPS = 1.25  # FP64 (CUDA-core and DMMA) nominal rate of GB300
+FP64_ALU_PEAK_TFLOPS = 1.26  # FP64 CUDA-core rate of GB300: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz
 
 
 def nominal_flops(n):
@@ -266,28 +266,33 @@ def ours(args):
            "columns_checked": int(len(cols))}
 
     # ---- roofline of the dominant kernel category
+    # Categories are "stage/engine" for products ("/tc_split": tensor-core split
+    # product, executed bf16 flops; "/fp64_simt", "/fp64_splitk": FP64 CUDA cores)
+    # and plain stage names for the other kernels.  Bulge chasing carries both its
+    # FP64 flop count and the byte model 16 b n^2 (+4 n^2 for U).
     peaks, peak_kind = load_peaks()
-    dom = max(st.items(), key=lambda kv: kv[1][0]) if st else None
+    dom = max(((k, v) for k, v in st.items() if not k.endswith("/tc_split_prep")), key=lambda kv: kv[1][0],
+              default=None) if st else None
     roof = None
     if dom:
         cat, (dms, dfl, dby, dca) = dom
         per_launch_ms = dms / max(dca, 1)
         traffic = committed_traffic(cat, n)
-        if cat.startswith("gemm_tc"):
-            pairs = st.get("_pairs", None)
+        secs = dms / 1e3
+        if cat.endswith("/tc_split"):
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-            roof = {"kernel": cat, "bound": "tensor", "achieved": dfl / (dms / 1e3) / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "traffic": traffic}
-        elif cat == "bc_chase":
-            peak = peaks.get("hbm_gbs")
-            roof = {"kernel": cat, "bound": "hbm", "achieved": dby / (dms / 1e3) / 1e9, "peak": peak,
-                    "unit": "GB/s", "traffic": traffic}
+            roof = {"kernel": cat, "bound": "tensor", "achieved": dfl / secs / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "traffic": traffic,
+                    "peak_source": f"{peak_kind} MEASURED_PEAKS.json bf16_tflops_sustained (executed bf16 flops "
+                                   f"of the slice-pair products)"}
         else:
-            roof = {"kernel": cat, "bound": "alu", "achieved": dfl / (dms / 1e3) / 1e12,
-                    "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": traffic}
+            roof = {"kernel": cat, "bound": "alu", "achieved": dfl / secs / 1e12, "peak": FP64_ALU_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "traffic": traffic,
+                    "peak_source": "FP64 CUDA-core rate 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s"}
+            if dby > 0:
+                roof["hbm_model_gbs"] = dby / secs / 1e9
+                roof["hbm_model_frac"] = roof["hbm_model_gbs"] / peaks.get("hbm_gbs")
         roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
-        roof["peak_source"] = (f"{peak_kind} MEASURED_PEAKS.json" if roof["bound"] != "alu"
-                               else "GB300 nominal FP64 rate (1.25 TFLOP/s)")
         roof["launches"] = int(dca)
         roof["ms_per_launch"] = per_launch_ms
         roof["share_of_step"] = dms / (ms * args.steps) if ms > 0 else None

@@ -184,7 +184,7 @@ evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char*
 /* ---------------------------------------------------------------------------
  * Instrumentation (off by default; used by the benchmark).  When enabled, the
  * library records CUDA events around its launches on the launching stream,
- * grouped by category ("gemm_fp64_simt", "gemm_tc_split", "sbr_panel_qr",
+ * grouped by category ("sbr_z/tc_split", "gemm/fp64_simt", "sbr_panel_qr",
  * "bc_chase", "dc_leaf", "dc_merge", "dc_secular", "bc_back", ...), together with
  * the algorithmic flops and bytes of each call.  The library also counts every
  * kernel it launches.  Host-side state, process-wide; not thread-safe across

@@ -594,7 +594,9 @@ evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, b
     void* args[] = {&a};
     // model bytes (each step reads and writes its 2b x b window; U written once)
     const double nn = (double)n * (double)n;
-    StatScope sc("bc_chase", s, 5.0 * pc.b * nn, 16.0 * pc.b * nn + (vectors ? 4.0 * nn : 0.0));
+    // FP64 flops: about 12 b^2 per step (left and right applications 4 b^2 each,
+    // symmetric mat-vec 2 b^2, rank-2 update 2 b^2) over n^2 / (2b) steps
+    StatScope sc("bc_chase", s, 6.0 * pc.b * nn, 16.0 * pc.b * nn + (vectors ? 4.0 * nn : 0.0));
     EVD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)G), dim3(nt), args, smem, s)); count_launch();
   }
   if (n > 0) {

@@ -166,7 +166,7 @@ evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes
       g.k >= 4 * SK_CHUNK && scratch) {
     const int nch = (int)ceil_div(g.k, SK_CHUNK);
     if (scratch_bytes >= (size_t)nch * g.m * g.n * sizeof(double)) {
-      StatScope sc("gemm_fp64_splitk", s, 2.0 * (double)g.m * (double)g.n * (double)g.k);
+      StatScope sc(g.tag ? g.tag : "gemm", s, 2.0 * (double)g.m * (double)g.n * (double)g.k, 0.0, "fp64_splitk");
       double* part = static_cast<double*>(scratch);
       k_atb_partial<<<nch, 256, 0, s>>>(g.A, g.lda, g.B, g.ldb, g.m, g.n, g.k, part); count_launch();
       k_atb_sum<<<(unsigned)ceil_div(g.m * g.n, 256), 256, 0, s>>>(part, nch, g.m, g.n, g.alpha, g.beta, g.C, g.ldc); count_launch();
@@ -177,7 +177,7 @@ evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes
   dim3 grid((unsigned)ceil_div(g.m, BM), (unsigned)ceil_div(g.n, BN));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
   const double flops = (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;
-  StatScope sc(g.tag ? g.tag : "gemm_fp64_simt", s, flops);
+  StatScope sc(g.tag ? g.tag : "gemm", s, flops, 0.0, "fp64_simt");
   k_dgemm_simt<<<grid, NT, 0, s>>>(g); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   return EVD_OK;

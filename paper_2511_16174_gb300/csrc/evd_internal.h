@@ -177,13 +177,16 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
 // launches on stream s under category `cat` and adds the algorithmic flops/bytes.
 class StatScope {
  public:
-  StatScope(const char* cat, cudaStream_t s, double flops = 0, double bytes = 0);
+  // The category key is cat, or "cat/engine" when engine is given (the engine a
+  // product ran on: "tc_split", "tc_split_prep", "fp64_simt", "fp64_splitk").
+  StatScope(const char* cat, cudaStream_t s, double flops = 0, double bytes = 0, const char* engine = nullptr);
   ~StatScope();
   StatScope(const StatScope&) = delete;
   StatScope& operator=(const StatScope&) = delete;
 
  private:
   const char* cat_;
+  const char* engine_ = nullptr;
   cudaStream_t s_;
   void* a_ = nullptr;
   bool on_ = false;

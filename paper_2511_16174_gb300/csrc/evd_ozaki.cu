@@ -766,9 +766,9 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
   vb.pstride = bt.sB;
   const double flops = (double)count * (g.lower ? 1.0 : 2.0) * (double)g.m * (double)g.n * (double)g.k;
   {
-    StatScope sc(g.tag ? "gemm_tc_split_prep_tagged" : "gemm_tc_split_prep", s, 0.0,
+    StatScope sc(g.tag ? g.tag : "gemm", s, 0.0,
                  (double)count * (8.0 * (double)(g.m + g.n) * (double)g.k * 2.0 +
-                                  2.0 * slices * (double)(p.m_pad + p.n_pad) * p.k_pad));
+                                  2.0 * slices * (double)(p.m_pad + p.n_pad) * p.k_pad), "tc_split_prep");
     dim3 blk(32, 8);
     if (p.k_pad <= 512) {
       static bool fused_attr = false;
@@ -829,7 +829,7 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
   }
   dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)(count > 1 ? count : zsplits));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
-  StatScope sc(g.tag ? g.tag : "gemm_tc_split", s, flops * (double)(slices * (slices + 1) / 2));
+  StatScope sc(g.tag ? g.tag : "gemm", s, flops * (double)(slices * (slices + 1) / 2), 0.0, "tc_split");
   k_ozaki_mma<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, a); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   if (zsplits > 1) {

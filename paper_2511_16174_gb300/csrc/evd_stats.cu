@@ -41,13 +41,25 @@ cudaEvent_t take_event() {
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-StatScope::StatScope(const char* cat, cudaStream_t s, double flops, double bytes) : cat_(cat), s_(s) {
+namespace {
+std::string key_of(const char* cat, const char* engine) {
+  std::string k(cat ? cat : "");
+  if (engine) {
+    k += '/';
+    k += engine;
+  }
+  return k;
+}
+}  // namespace
+
+StatScope::StatScope(const char* cat, cudaStream_t s, double flops, double bytes, const char* engine)
+    : cat_(cat), engine_(engine), s_(s) {
   on_ = g_on.load(std::memory_order_relaxed);
   if (!on_) return;
   std::lock_guard<std::mutex> lk(g_mu);
   a_ = take_event();
   cudaEventRecord(static_cast<cudaEvent_t>(a_), s_);
-  Cat& c = g_cats[cat_];
+  Cat& c = g_cats[key_of(cat_, engine_)];
   c.flops += flops;
   c.bytes += bytes;
   c.calls += 1;
@@ -58,7 +70,7 @@ StatScope::~StatScope() {
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = take_event();
   cudaEventRecord(b, s_);
-  g_cats[cat_].recs.push_back({static_cast<cudaEvent_t>(a_), b});
+  g_cats[key_of(cat_, engine_)].recs.push_back({static_cast<cudaEvent_t>(a_), b});
 }
 
 }  // namespace evd

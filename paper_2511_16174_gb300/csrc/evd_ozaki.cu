@@ -21,23 +21,26 @@
 // C = alpha (2^(e_r + f_c - 14 - 7H) R_hi + 2^(e_r + f_c - 14 - 7(s-1)) R_lo) + beta C
 // in FP64.
 //
+// Slice layout ("blobs"): the split kernels write each operand as blobs, one per
+// (row tile, K-block of 16): s slices x TR rows x 16 K-elements (TR = 128 for the
+// left operand, 64 for the right), each slice in the tensor core's canonical
+// K-major layout without swizzle -- core matrices of 8 rows x 8 elements (128 bytes)
+// ordered (row group, K half).  A stage of the product is then one contiguous bulk
+// copy per operand (s x 4 KB and s x 2 KB) instead of a box of 32-byte rows.
+//
 // Kernel structure (one CTA per 128 x 64 tile of C, 320 threads):
-//   warp 0      TMA producer: one 3-D box per operand and stage carries all s
-//               slices (16 K-elements, 32-byte rows, 32-byte swizzle), 4 stages.
+//   warp 0      copy producer: one bulk copy per operand and stage, 4 stages.
 //   warp 1      tensor-memory allocation (512 columns) and the single MMA-issuing
 //               thread: per stage, every slice pair (t, u) with t + u <= s-1.
 //   warps 2..9  epilogue: drains all weight accumulators every 16 stages into
 //               int64 registers, then the FP64 write of C.
 // Every mbarrier wait is bounded; on timeout the CTA raises the abort flag, sets
 // EVD_ERR_TIMEOUT in the status word and leaves after freeing tensor memory.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "device_util.cuh"
 #include "evd_ozaki.h"
@@ -75,6 +78,14 @@ struct View {
   }
   __device__ __forceinline__ bool row_contig() const { return mode != 1; }
 };
+
+// Element index of (row R, K-element k) of slice t in the blob layout with TR-row
+// tiles and nkb K-blocks per row tile (R counts rows over all batched problems).
+__device__ __forceinline__ size_t blob_index(int64_t R, int64_t k, int t, int s, int TR, int64_t nkb) {
+  const int64_t tile = R / TR, rr = R - tile * TR, kb = k >> 4, kk = k & 15;
+  return ((size_t)(tile * nkb + kb) * s + t) * (size_t)(TR * 16) + (size_t)(((rr >> 3) * 2 + (kk >> 3)) * 64) +
+         (size_t)((rr & 7) * 8 + (kk & 7));
+}
 
 __device__ __forceinline__ void load_tile32(const View& v, int64_t r0, int64_t k0, double (*t)[33]) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -146,7 +157,7 @@ __device__ __forceinline__ int ozaki_digit(long long TO, int s, int t) {
 // Slices S[t][rho][kappa] (bfloat16, K-major, rows_pad x K_pad per slice) and the
 // frexp exponent per row (ex holds the max biased exponent on entry).
 __global__ void k_split(const View v, const int* ex_biased, int* ex_frexp, int s, int64_t rows_pad, int64_t K_pad,
-                        __nv_bfloat16* S) {
+                        __nv_bfloat16* S, int TR) {
   __shared__ double t[32][33];
   const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
   load_tile32(v, r0, k0, t);
@@ -162,11 +173,12 @@ __global__ void k_split(const View v, const int* ex_biased, int* ex_frexp, int s
     const long long off = ozaki_offset(s);
     const long long T0 = ozaki_scaled(t[rr][2 * q], e, s) + off;
     const long long T1 = ozaki_scaled(t[rr][2 * q + 1], e, s) + off;
+    const int64_t nkb = K_pad / 16;
     for (int tt = 0; tt < s; ++tt) {
       __nv_bfloat162 h;
       h.x = __float2bfloat16_rn((float)ozaki_digit(T0, s, tt));
       h.y = __float2bfloat16_rn((float)ozaki_digit(T1, s, tt));
-      *reinterpret_cast<__nv_bfloat162*>(S + ((size_t)tt * rows_pad + R) * K_pad + k0 + 2 * q) = h;
+      *reinterpret_cast<__nv_bfloat162*>(S + blob_index(R, k0 + 2 * q, tt, s, TR, nkb)) = h;
     }
   }
 }
@@ -187,8 +199,10 @@ __global__ void __launch_bounds__(256) k_split_fused(const View va, int* ea, __n
   if (pb == 0 && v.K0 >= 0) v.K = v.K0;
   const int64_t rows_pad = isA ? rows_pad_a : rows_pad_b;
   int* ex = (isA ? ea : eb) + pb * rows_pad;
-  __nv_bfloat16* S = (isA ? SA : SB) + pb * rows_pad * K_pad;
-  const int64_t slice_stride = count * rows_pad * K_pad;
+  __nv_bfloat16* S = isA ? SA : SB;
+  const int TR = isA ? 128 : 64;
+  const int64_t nkb = K_pad / 16;
+  (void)count;
   const int64_t r0 = (int64_t)(isA ? (int)blockIdx.x : (int)blockIdx.x - nblk_a) * 32;
   const int ls = (int)K_pad + 1;
   const int tid = threadIdx.x;
@@ -236,7 +250,7 @@ __global__ void __launch_bounds__(256) k_split_fused(const View va, int* ea, __n
         h.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * i + 1], s, tt));
         w[i] = *reinterpret_cast<uint32_t*>(&h);
       }
-      *reinterpret_cast<uint4*>(S + (size_t)tt * slice_stride + (size_t)R * K_pad + 8 * u) =
+      *reinterpret_cast<uint4*>(S + blob_index(pb * rows_pad + R, 8 * u, tt, s, TR, nkb)) =
           make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
@@ -274,27 +288,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile 
   dev_set_status(st, EVD_ERR_TIMEOUT, where);
   return false;
 }
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
-                                            uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
-      : "memory");
+// Contiguous global -> shared bulk copy completing on an mbarrier (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mbar)
+               : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
-// K-major operand tile, 32-byte rows, 32-byte swizzle: SBO = 8 rows x 32 B.
-__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
+// K-major operand without swizzle: core matrices of 8 rows x 16 bytes stored as
+// 128 contiguous bytes; the two core matrices of a 16-element K step are 128 bytes
+// apart (leading byte offset), consecutive 8-row groups 256 bytes apart (stride
+// byte offset).
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(256 >> 4) << 32;    // stride byte offset: 8 rows x 32 B
+  d |= (uint64_t)(128 >> 4) << 16;    // leading byte offset: next core matrix along K
+  d |= (uint64_t)(256 >> 4) << 32;    // stride byte offset: next 8-row group
   d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
-  d |= (uint64_t)6 << 61;             // 32-byte swizzle
-  return d;
+  return d;                           // layout type 0: no swizzle
 }
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
@@ -370,6 +386,9 @@ __device__ __forceinline__ double i128_to_double(long long hi, unsigned long lon
 }
 
 struct MmaArgs {
+  const __nv_bfloat16* SA;  // left operand blobs
+  const __nv_bfloat16* SB;  // right operand blobs
+  int64_t nkb;              // K-blocks of 16 per row tile
   int64_t m, n;
   int s;            // slices
   int nst;          // stages = K_pad / OZ_KS
@@ -394,7 +413,7 @@ __device__ __forceinline__ bool drain_after(int j, int nst) {
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_ozaki_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const MmaArgs a) {
+    k_ozaki_mma(const MmaArgs a) {
   extern __shared__ uint8_t smem_raw[];
   // grouped rasterization: consecutive CTAs sweep OZ_GROUP_M row tiles for each
   // column tile, so a wave shares both operands' slices in L2
@@ -412,7 +431,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int64_t pb = a.batched ? (int64_t)blockIdx.z : 0;
   const int j0 = a.batched ? 0 : (int)blockIdx.z * a.stages_per_split;
   const int nst = (a.nst - j0 < a.stages_per_split) ? a.nst - j0 : a.stages_per_split;
-  const int rowA = (int)(pb * a.bm_pad + m0), rowB = (int)(pb * a.bn_pad + n0);
+  // blobs of this CTA's row tiles: stage j reads K-block j0 + j
+  const __nv_bfloat16* blobA = a.SA + (size_t)((pb * a.bm_pad + m0) / OZ_BM) * a.nkb * s * (OZ_BM * OZ_KS);
+  const __nv_bfloat16* blobB = a.SB + (size_t)((pb * a.bn_pad + n0) / OZ_BN) * a.nkb * s * (OZ_BN * OZ_KS);
   const int* ea = a.ea + pb * a.bm_pad;
   const int* eb = a.eb + pb * a.bn_pad;
   double* Cp = a.C + pb * a.sC;
@@ -450,8 +471,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
       int issued = 0;
       for (int j = 0; j < nst; ++j) {
         const int si = j % OZ_STAGES, round = j / OZ_STAGES;
@@ -459,8 +478,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         uint8_t* sa = smem + si * stage_bytes;
         const uint32_t fb = smem_u32(full + si);
         mbar_expect_tx(fb, stage_bytes);
-        tma_load_3d(smem_u32(sa), &tmA, (j0 + j) * OZ_KS, rowA, 0, fb);
-        tma_load_3d(smem_u32(sa + a_bytes), &tmB, (j0 + j) * OZ_KS, rowB, 0, fb);
+        bulk_load(smem_u32(sa), blobA + (size_t)(j0 + j) * s * (OZ_BM * OZ_KS), a_bytes, fb);
+        bulk_load(smem_u32(sa + a_bytes), blobB + (size_t)(j0 + j) * s * (OZ_BN * OZ_KS), b_bytes, fb);
         ++issued;
       }
       if (*abort) {
@@ -492,10 +511,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const uint32_t sb = sa + a_bytes;
         for (int t = 0; t <= L; ++t) {
           const int nu = L - t + 1;  // u = 0 .. L - t
-          const uint64_t da = desc_sw32(sa + (uint32_t)t * OZ_BM * OZ_KS * 2);
+          const uint64_t da = desc_kmajor(sa + (uint32_t)t * OZ_BM * OZ_KS * 2);
           for (int u0 = 0; u0 < nu; u0 += 4) {
             const int cnt = (nu - u0 < 4) ? nu - u0 : 4;
-            const uint64_t db = desc_sw32(sb + (uint32_t)u0 * OZ_BN * OZ_KS * 2);
+            const uint64_t db = desc_kmajor(sb + (uint32_t)u0 * OZ_BN * OZ_KS * 2);
             tc_mma(tmem + (uint32_t)((t + u0) * OZ_BN), da, db, idesc[cnt - 1], (fresh && t == 0) ? 0u : 1u);
           }
         }
@@ -628,61 +647,6 @@ __global__ void k_splitk_reduce(const double* part, int splits, int64_t m, int64
 }
 
 // ------------------------------------------------------------------ host side
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-// 3-D map over S[s][rows_pad][K_pad] (bf16), box {16, box_rows, s}, 32-byte swizzle.
-// Encoded maps are cached by (base, extents, box): the slice buffers of a plan's
-// workspace are reused call after call, and encoding is a host-side cost.
-struct MapKey {
-  void* base;
-  int64_t K_pad, rows_pad;
-  int s, box_rows;
-};
-constexpr int kMapCache = 64;
-MapKey g_map_keys[kMapCache];
-CUtensorMap g_maps[kMapCache];
-int g_map_n = 0, g_map_next = 0;
-std::mutex g_map_mu;
-
-bool make_map_uncached(CUtensorMap* tm, void* base, int64_t K_pad, int64_t rows_pad, int s, int box_rows);
-bool make_map(CUtensorMap* tm, void* base, int64_t K_pad, int64_t rows_pad, int s, int box_rows) {
-  std::lock_guard<std::mutex> lk(g_map_mu);
-  for (int i = 0; i < g_map_n; ++i) {
-    const MapKey& k = g_map_keys[i];
-    if (k.base == base && k.K_pad == K_pad && k.rows_pad == rows_pad && k.s == s && k.box_rows == box_rows) {
-      *tm = g_maps[i];
-      return true;
-    }
-  }
-  if (!make_map_uncached(tm, base, K_pad, rows_pad, s, box_rows)) return false;
-  const int slot = (g_map_n < kMapCache) ? g_map_n++ : (g_map_next++ % kMapCache);
-  g_map_keys[slot] = {base, K_pad, rows_pad, s, box_rows};
-  g_maps[slot] = *tm;
-  return true;
-}
-
-bool make_map_uncached(CUtensorMap* tm, void* base, int64_t K_pad, int64_t rows_pad, int s, int box_rows) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)K_pad, (cuuint64_t)rows_pad, (cuuint64_t)s};
-  cuuint64_t strides[2] = {(cuuint64_t)K_pad * 2, (cuuint64_t)rows_pad * K_pad * 2};
-  cuuint32_t box[3] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, (cuuint32_t)s};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 struct Pads {
   int64_t m_pad, n_pad, k_pad;
 };
@@ -787,17 +751,14 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
       k_row_exponent<<<dim3((unsigned)ceil_div(g.m, 32), (unsigned)ceil_div(g.k, kspan)), blk, 0, s>>>(va, exA, kspan); count_launch();
       k_row_exponent<<<dim3((unsigned)ceil_div(g.n, 32), (unsigned)ceil_div(g.k, kspan)), blk, 0, s>>>(vb, exB, kspan); count_launch();
       k_split<<<dim3((unsigned)(p.m_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(va, exA, eA, slices, p.m_pad,
-                                                                                     p.k_pad, SA); count_launch();
+                                                                                     p.k_pad, SA, OZ_BM); count_launch();
       k_split<<<dim3((unsigned)(p.n_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(vb, exB, eB, slices, p.n_pad,
-                                                                                     p.k_pad, SB); count_launch();
+                                                                                     p.k_pad, SB, OZ_BN); count_launch();
     }
     EVD_CUDA_TRY(cudaGetLastError());
   }
-  CUtensorMap tmA, tmB;
-  if (!make_map(&tmA, SA, p.k_pad, count * p.m_pad, slices, OZ_BM) ||
-      !make_map(&tmB, SB, p.k_pad, count * p.n_pad, slices, OZ_BN))
-    return EVD_ERR_CUDA;
   MmaArgs a;
+  a.SA = SA; a.SB = SB; a.nkb = p.k_pad / OZ_KS;
   a.m = g.m; a.n = g.n; a.s = slices; a.nst = (int)(p.k_pad / OZ_KS);
   uint32_t cols = 64;
   while (cols < (uint32_t)(slices * OZ_BN)) cols <<= 1;
@@ -830,7 +791,7 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
   dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)(count > 1 ? count : zsplits));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
   StatScope sc(g.tag ? g.tag : "gemm", s, flops * (double)(slices * (slices + 1) / 2), 0.0, "tc_split");
-  k_ozaki_mma<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, a); count_launch();
+  k_ozaki_mma<<<grid, OZ_THREADS, smem, s>>>(a); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   if (zsplits > 1) {
     for (int64_t j0 = 0; j0 < g.n; j0 += 65535) {

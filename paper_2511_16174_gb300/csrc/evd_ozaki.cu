@@ -11,8 +11,8 @@
 // weight, weight k at columns 64 k).  One instruction multiplies slice t of A by
 // up to four consecutive slices u0..u0+3 of B stacked along N (N <= 256), which
 // lands in the accumulators of weights t+u0..t+u0+3 -- 12 instructions per K-step
-// instead of 36.  The accumulators are drained every 256 K-elements; a weight-k
-// accumulator then never exceeds (k+3) 2^12 * 256 <= 2^24 in magnitude,
+// instead of 36.  The accumulators are drained every 384 K-elements; a weight-k
+// accumulator then never exceeds (k+3) 2^12 * 384 < 2^24 in magnitude (k <= 7),
 // so every partial sum is an exact integer; drains are converted to int64 and
 // combined exactly, with left shifts only, into two accumulators
 //     R_hi = sum_{k <= H} S_k 2^(7 (H - k))      H = min(s-1, 3)
@@ -55,7 +55,7 @@ constexpr int OZ_KS = 16;         // K-elements per stage (one MMA K-step, 32-by
 constexpr int OZ_MAXS = 8;        // slices
 constexpr int OZ_STAGES = 4;
 constexpr int OZ_THREADS = 320;
-constexpr int OZ_PERIOD = 16;     // stages between two drains of one weight (256 K-elements)
+constexpr int OZ_PERIOD = 24;     // stages between two drains of one weight (384 K-elements)
 constexpr long long OZ_WAIT_LIMIT = 1ll << 26;
 constexpr int OZ_GROUP_M = 8;     // row tiles per rasterization group
 constexpr uint32_t OZ_PARK_BYTES = 256 * 64 * 8;  // epilogue: 2 x 32 int64 sums per epilogue thread
@@ -408,10 +408,32 @@ struct MmaArgs {
   int64_t bm_pad, bn_pad, sC, m_first;
 };
 
+// All slice-pair products of one K-step for S slices: for each A slice t, the B
+// slices u = 0 .. S-1-t in groups of up to four stacked along N (N <= 256), into the
+// weight accumulators t+u0 .. at TMEM columns 64 (t + u0).  Fully unrolled: every
+// descriptor is the stage's base descriptor plus a constant (the 14-bit address
+// field cannot carry: shared-memory addresses stay below 2^18 bytes).  The first
+// products into each weight (t = 0) take acc_t0 (0 at the start of a drain chunk).
+template <int S>
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t da0, uint64_t db0, uint32_t acc_t0) {
+  constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+#pragma unroll
+    for (int u0 = 0; u0 < S - t; u0 += 4) {
+      const int cnt = (S - t - u0 < 4) ? S - t - u0 : 4;
+      tc_mma(tmem + (uint32_t)((t + u0) * OZ_BN), da0 + (uint64_t)((t * OZ_BM * OZ_KS * 2) >> 4),
+             db0 + (uint64_t)((u0 * OZ_BN * OZ_KS * 2) >> 4),
+             kIdesc | ((uint32_t)((OZ_BN * cnt) >> 3) << 17), t == 0 ? acc_t0 : 1u);
+    }
+  }
+}
+
 __device__ __forceinline__ bool drain_after(int j, int nst) {
   return (j % OZ_PERIOD == OZ_PERIOD - 1) || (j == nst - 1);
 }
 
+template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki_mma(const MmaArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -427,7 +449,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int64_t m0 = (int64_t)mt * OZ_BM, n0 = (int64_t)nt * OZ_BN;
   if (a.lower && n0 > m0 + OZ_BM - 1) return;  // tile strictly above the diagonal
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const int s = a.s, L = s - 1;
+  constexpr int s = S, L = S - 1;
   const int64_t pb = a.batched ? (int64_t)blockIdx.z : 0;
   const int j0 = a.batched ? 0 : (int)blockIdx.z * a.stages_per_split;
   const int nst = (a.nst - j0 < a.stages_per_split) ? a.nst - j0 : a.stages_per_split;
@@ -493,11 +515,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      uint32_t idesc[4];
-      for (int q = 0; q < 4; ++q)
-        idesc[q] = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((OZ_BN * (q + 1)) >> 3) << 17) |
-                   ((uint32_t)(OZ_BM >> 4) << 24);
       int chunk = 0;
+      const uint64_t da_base = desc_kmajor(smem_u32(smem));
       for (int j = 0; j < nst && !*abort; ++j) {
         const int si = j % OZ_STAGES, round = j / OZ_STAGES;
         if (!mbar_wait(smem_u32(full + si), round & 1, abort, a.st, 9002)) break;
@@ -507,17 +526,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           if (!mbar_wait(smem_u32(acce), (chunk - 1) & 1, abort, a.st, 9003)) break;
           tc_fence_after();
         }
-        const uint32_t sa = smem_u32(smem + si * stage_bytes);
-        const uint32_t sb = sa + a_bytes;
-        for (int t = 0; t <= L; ++t) {
-          const int nu = L - t + 1;  // u = 0 .. L - t
-          const uint64_t da = desc_kmajor(sa + (uint32_t)t * OZ_BM * OZ_KS * 2);
-          for (int u0 = 0; u0 < nu; u0 += 4) {
-            const int cnt = (nu - u0 < 4) ? nu - u0 : 4;
-            const uint64_t db = desc_kmajor(sb + (uint32_t)u0 * OZ_BN * OZ_KS * 2);
-            tc_mma(tmem + (uint32_t)((t + u0) * OZ_BN), da, db, idesc[cnt - 1], (fresh && t == 0) ? 0u : 1u);
-          }
-        }
+        const uint64_t da0 = da_base + (uint64_t)((si * stage_bytes) >> 4);
+        const uint64_t db0 = da0 + (uint64_t)(a_bytes >> 4);
+        issue_stage<S>(tmem, da0, db0, fresh ? 0u : 1u);
         if (drain_after(j, nst)) {
           tc_commit(smem_u32(accf));
           ++chunk;
@@ -647,6 +658,18 @@ __global__ void k_splitk_reduce(const double* part, int splits, int64_t m, int64
 }
 
 // ------------------------------------------------------------------ host side
+const void* mma_kernel(int slices) {
+  switch (slices) {
+    case 1: return (const void*)k_ozaki_mma<1>;
+    case 2: return (const void*)k_ozaki_mma<2>;
+    case 3: return (const void*)k_ozaki_mma<3>;
+    case 4: return (const void*)k_ozaki_mma<4>;
+    case 5: return (const void*)k_ozaki_mma<5>;
+    case 6: return (const void*)k_ozaki_mma<6>;
+    case 7: return (const void*)k_ozaki_mma<7>;
+    default: return (const void*)k_ozaki_mma<8>;
+  }
+}
 struct Pads {
   int64_t m_pad, n_pad, k_pad;
 };
@@ -784,14 +807,16 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
   const size_t smem = smem_bytes(slices);
   static bool attr_set = false;
   if (!attr_set) {
-    EVD_CUDA_TRY(cudaFuncSetAttribute(k_ozaki_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_bytes(OZ_MAXS)));
+    for (int q = 1; q <= OZ_MAXS; ++q)
+      EVD_CUDA_TRY(cudaFuncSetAttribute(mma_kernel(q), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_bytes(OZ_MAXS)));
     attr_set = true;
   }
   dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)(count > 1 ? count : zsplits));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
   StatScope sc(g.tag ? g.tag : "gemm", s, flops * (double)(slices * (slices + 1) / 2), 0.0, "tc_split");
-  k_ozaki_mma<<<grid, OZ_THREADS, smem, s>>>(a); count_launch();
+  void* kargs[] = {&a};
+  EVD_CUDA_TRY(cudaLaunchKernel(mma_kernel(slices), grid, dim3(OZ_THREADS), kargs, smem, s)); count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
   if (zsplits > 1) {
     for (int64_t j0 = 0; j0 < g.n; j0 += 65535) {

@@ -53,7 +53,7 @@ typedef enum { EVD_VALUES = 0, EVD_VECTORS = 1 } evd_job_t;
  *   EVD_FP64        FP64-accurate products: FP64 operands split into 8 bfloat16
  *                   slices of 7 bits, slice pairs multiplied on tensor cores with
  *                   exact FP32 partial sums, recombined in 64-bit integers.
- *   EVD_SPLIT_BF16  Split precision: 4 slices for those products, then
+ *   EVD_SPLIT_BF16  Split precision: 6 slices for those products, then
  *                   Ogita-Aishima refinement with FP64-accurate residual products.
  *   EVD_SPLIT_INT8  Accepted for interface completeness; GB300's INT8 tensor rate
  *                   is far below its BF16 rate, so this returns EVD_ERR_NOT_SUPPORTED.

@@ -15,6 +15,11 @@ eigenvector matrix X:
 The 2-norms in delta are replaced by Frobenius norms, which bound them from above
 (so the threshold can only grow; clustered pairs then fall into the r_ij/2 branch,
 which is the safe one).  Matrix products are numpy's FP64 matmul.
+
+R and S are symmetric by definition; the computed products are replaced by their
+symmetric parts (R + R^T)/2, (S + S^T)/2.  Without that, E_ij + E_ji = r_ij +
+(s_ij - s_ji)/(lam_j - lam_i) carries the rounding asymmetry of S divided by the
+eigenvalue gap, and the orthogonality of X stalls near 1e-12 in FP64.
 """
 from __future__ import annotations
 
@@ -28,6 +33,8 @@ def refine(A, X):
     n = A.shape[0]
     R = np.eye(n) - X.T @ X
     S = X.T @ (A @ X)
+    R = 0.5 * (R + R.T)
+    S = 0.5 * (S + S.T)
     r = np.diag(R)
     lam = np.diag(S) / (1.0 - r)
     D = S - np.diag(lam)

@@ -215,6 +215,44 @@ int default_b(int64_t n) { return n >= 4096 ? 64 : 32; }
 
 }  // namespace
 
+namespace evd {
+
+// The plan's tunables.  b = nb = 0: the autotuner's cached choice (file named by
+// EVD_AUTOTUNE_CACHE) if there is one, else b = 64 for n >= 4096 and 32 below,
+// nb = b.  b > 0, nb = 0: nb = b.
+void fill_core(PlanCore& c, int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb) {
+  c.n = n;
+  c.lda = lda;
+  c.job = job;
+  c.prec = prec;
+  int tb = 0, tnb = 0;
+  if (b == 0 && nb == 0 && autotune_lookup(n, job, prec, &tb, &tnb)) {
+    c.b = tb;
+    c.nb = tnb;
+  } else {
+    c.b = (b > 0) ? b : default_b(n);
+    if (c.b < 2 && b == 0) c.b = 2;
+    c.nb = (nb > 0) ? nb : c.b;
+  }
+  // split precision: 6 slices (21 slice pairs instead of 36) leave the eigenvectors
+  // accurate enough (about 1e-11 at n ~ 1e3) for two refinement steps to resolve
+  // clusters of gap 1e-6; with 4 slices (about 1e-7) such clusters stay mixed.
+  c.slices = (prec == EVD_SPLIT_BF16) ? 6 : 8;
+  c.ref_slices = 8;
+  c.refine_iters = (prec == EVD_SPLIT_BF16) ? 2 : 0;
+  if (const char* s = getenv("EVD_SLICES")) c.slices = atoi(s);
+  if (const char* s = getenv("EVD_REFINE_ITERS")) c.refine_iters = std::max(0, atoi(s));
+  if (const char* s = getenv("EVD_PANEL_CTAS")) c.panel_ctas = std::max(1, atoi(s));
+}
+
+size_t plan_workspace_bytes(int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb) {
+  PlanCore c;
+  fill_core(c, n, lda, job, prec, b, nb);
+  return make_layout(c, nullptr).total;
+}
+
+}  // namespace evd
+
 extern "C" {
 
 const char* evd_status_string(evd_status_t s) {
@@ -246,19 +284,8 @@ evd_status_t evd_plan_create(evd_plan_t* plan, int64_t n, int64_t lda, evd_job_t
   evd_plan_s* p = new (std::nothrow) evd_plan_s();
   if (!p) return EVD_ERR_OOM;
   PlanCore& c = p->core;
-  c.n = n;
-  c.lda = lda;
-  c.job = job;
-  c.prec = prec;
-  c.b = (b > 0) ? b : default_b(n);
-  if (c.b < 2 && b == 0) c.b = 2;
-  c.nb = (nb > 0) ? nb : c.b;
-  c.slices = (prec == EVD_SPLIT_BF16) ? 4 : 8;
-  c.ref_slices = 8;
-  c.refine_iters = (prec == EVD_SPLIT_BF16) ? 2 : 0;
+  fill_core(c, n, lda, job, prec, b, nb);
   c.stream = static_cast<cudaStream_t>(stream);
-  if (const char* s = getenv("EVD_SLICES")) c.slices = atoi(s);
-  if (const char* s = getenv("EVD_PANEL_CTAS")) c.panel_ctas = std::max(1, atoi(s));
   cudaGetDevice(&c.device);
   cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device);
   if (cudaMalloc(&p->d_status, sizeof(int) * kStatusWords) != cudaSuccess ||

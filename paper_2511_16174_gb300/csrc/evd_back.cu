@@ -172,8 +172,10 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   if (n < 3 || pc.b < 2) return EVD_OK;
   const int b = pc.b, g = pc.b;
   const int h = g + b - 1;
-  // small problems: reflector-by-reflector kernel on FP64 cores
-  if (pc.slices <= 0 || n < 1024 || !w.Vg) {
+  const size_t smem = ((size_t)h * g + (size_t)g * g + 2 * g) * sizeof(double);
+  // small problems, and band widths whose group factors do not fit in shared
+  // memory (b > 64): reflector-by-reflector kernel on FP64 cores
+  if (pc.slices <= 0 || n < 1024 || !w.Vg || smem > kMaxDynamicSmem) {
     const unsigned grid = (unsigned)ceil_div(n, BB_NC);
     StatScope sc("bc_back", pc.stream, 4.0 * pc.b * (double)n * (double)bc_num_reflectors(n, pc.b));
     k_bc_back<<<grid, BB_NT, 0, pc.stream>>>(bw.U, bw.Utau, n, pc.b, pc.b, Q, ldq); count_launch();
@@ -183,11 +185,9 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   cudaStream_t s = pc.stream;
   const int64_t nsweeps = n - 2;
   const int64_t nJ = ceil_div(nsweeps, g);
-  const size_t smem = ((size_t)h * g + (size_t)g * g + 2 * g) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    EVD_CUDA_TRY(cudaFuncSetAttribute(k_bcback_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    const evd_status_t st = ensure_dynamic_smem((const void*)k_bcback_prep, smem);
+    if (st != EVD_OK) return st;
   }
   auto kc = [&](int64_t J) { return sweep_steps_b(n, b, J * g); };
   const int64_t tmax = kc(0) + nJ - 2;
@@ -201,7 +201,8 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
       while (jp >= 0 && t - jp < kc(nJ - 1 - jp)) --jp;
       const int64_t jlo = jp + 1;
       const int count = (int)(jhi - jlo + 1);
-      if ((size_t)count * h * g > w.vg_capacity || (size_t)count * n * g > w.wt_capacity) return EVD_ERR_WORKSPACE;
+      if ((size_t)count * h * g > w.vg_capacity || (size_t)count * n * g > w.wt_capacity)
+        return ws_fail("bc_back wave buffers", w.wt_capacity, (size_t)count * n * g);
       {
         StatScope sc("bc_back_prep", s);
         k_bcback_prep<<<(unsigned)count, dim3(32, 8), smem, s>>>(bw.U, bw.Utau, n, b, g, nJ, t, jlo, w.Vg, w.Yg, h); count_launch();

@@ -587,7 +587,10 @@ evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, b
       smem = 3 * 64 * 65 * sizeof(double);
       nt = (variant == 2) ? 256 : BC_NT;
     }
-    if (smem > 48 * 1024) EVD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) {
+      const evd_status_t st = ensure_dynamic_smem(kern, smem);
+      if (st != EVD_OK) return st;
+    }
     int maxG = max_coresident_blocks(kern, nt, smem);
     int64_t G = n - 2;
     if (G > maxG) G = maxG;

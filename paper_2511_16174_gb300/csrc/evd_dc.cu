@@ -515,7 +515,7 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
   double* d_tol = reinterpret_cast<double*>(carve(sizeof(double) * (nmerge + 1)));
   int* d_k = reinterpret_cast<int*>(carve(sizeof(int) * (nmerge + 1)));
   int* d_nrot = reinterpret_cast<int*>(carve(sizeof(int) * (nmerge + 1)));
-  if (mb > ((size_t)24 * n + 1024) * sizeof(int)) return EVD_ERR_WORKSPACE;
+  if (mb > ((size_t)24 * n + 1024) * sizeof(int)) return ws_fail("dc merge descriptors", ((size_t)24 * n + 1024) * sizeof(int), mb);
   if (nmerge) EVD_CUDA_TRY(cudaMemcpyAsync(d_md, all.data(), sizeof(MergeDesc) * nmerge, cudaMemcpyHostToDevice, s));
   EVD_CUDA_TRY(cudaMemcpyAsync(d_loff, loff.data(), sizeof(int64_t) * nleaves, cudaMemcpyHostToDevice, s));
   EVD_CUDA_TRY(cudaMemcpyAsync(d_ln, ln.data(), sizeof(int) * nleaves, cudaMemcpyHostToDevice, s));

@@ -26,6 +26,10 @@ constexpr long long kSpinLimit = 16ll * 1000 * 1000;
   } while (0)
 
 evd_status_t cuda_fail(cudaError_t e, const char* what);
+// EVD_ERR_WORKSPACE, with a note on stderr when EVD_DEBUG is set.
+evd_status_t ws_fail(const char* where, size_t have, size_t need);
+evd_status_t ensure_dynamic_smem(const void* func, size_t bytes);
+constexpr size_t kMaxDynamicSmem = 227 * 1024;  // per CTA on sm_103
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -124,6 +128,11 @@ struct BcWork {
   unsigned* bar;
 };
 int64_t bc_num_reflectors(int64_t n, int b);
+// Plan tunables and workspace size without creating a plan (evd_api.cu).
+void fill_core(PlanCore& c, int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb);
+size_t plan_workspace_bytes(int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb);
+// Autotuner cache lookup for plans created with b = nb = 0 (evd_batched.cu).
+bool autotune_lookup(int64_t n, evd_job_t job, evd_prec_t prec, int* b, int* nb);
 // Upper bound on the number of reflector groups in one BC-Back wave (groups of a
 // wave start 2b rows apart, all below row n).
 int64_t bc_wave_max_groups(int64_t n, int b);

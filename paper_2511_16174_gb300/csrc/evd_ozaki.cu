@@ -688,10 +688,6 @@ int splitk_count(int64_t m, int64_t n, int64_t k) {
   if (m * n * sp > ((int64_t)1 << 27)) sp = std::max<int64_t>(1, ((int64_t)1 << 27) / (m * n));
   return (int)std::max<int64_t>(sp, 1);
 }
-size_t splitk_bytes(int64_t m, int64_t n, int64_t k) {
-  const int sp = splitk_count(m, n, k);
-  return sp > 1 ? (size_t)sp * m * n * sizeof(double) : 0;
-}
 
 size_t smem_bytes(int s) {
   const size_t stages = (size_t)OZ_STAGES * s * (OZ_BM + OZ_BN) * OZ_KS * 2;
@@ -700,7 +696,8 @@ size_t smem_bytes(int s) {
 
 }  // namespace
 
-size_t ozaki_scratch_bytes_batched(int64_t m, int64_t n, int64_t k, int slices, int count) {
+// Scratch of a (batched) product with `splits` K-splits (partials only when > 1).
+size_t scratch_with_splits(int64_t m, int64_t n, int64_t k, int slices, int count, int splits) {
   if (slices <= 0 || count <= 0) return 0;
   Pads p = pads(m, n, k);
   Carver c(nullptr);
@@ -710,8 +707,14 @@ size_t ozaki_scratch_bytes_batched(int64_t m, int64_t n, int64_t k, int slices, 
   c.take<int>((size_t)p.n_pad);
   c.take<int>((size_t)count * p.m_pad);
   c.take<int>((size_t)count * p.n_pad);
-  c.take<double>(count == 1 ? splitk_bytes(m, n, k) / sizeof(double) : 0);
+  c.take<double>(splits > 1 ? (size_t)splits * m * n : 0);
   return c.off + 256;
+}
+
+// The scratch a product prefers (with its preferred K-split count).  A smaller
+// scratch down to the no-split size also works: the split count is then lowered.
+size_t ozaki_scratch_bytes_batched(int64_t m, int64_t n, int64_t k, int slices, int count) {
+  return scratch_with_splits(m, n, k, slices, count, count == 1 ? splitk_count(m, n, k) : 1);
 }
 
 size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
@@ -730,7 +733,8 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
   const int count = bt.count;
   if (count < 1 || count > 65535) return EVD_ERR_INVALID_ARG;
   if (count > 1 && (g.lower || g.a_sym_lower)) return EVD_ERR_INVALID_ARG;
-  if (scratch_bytes < ozaki_scratch_bytes_batched(g.m, g.n, g.k, slices, count) || !scratch) return EVD_ERR_WORKSPACE;
+  if (!scratch || scratch_bytes < scratch_with_splits(g.m, g.n, g.k, slices, count, 1))
+    return ws_fail(g.tag ? g.tag : "split product", scratch_bytes, scratch_with_splits(g.m, g.n, g.k, slices, count, 1));
   if (g.k > ((int64_t)1 << 17)) return EVD_ERR_NOT_SUPPORTED;  // exactness bound of the int64 sums
   const Pads p = pads(g.m, g.n, g.k);
   if (count > 1 && p.k_pad > 512) return EVD_ERR_NOT_SUPPORTED;  // batched products use the one-pass split
@@ -742,8 +746,9 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
   int* exB = c.take<int>((size_t)p.n_pad);
   int* eA = c.take<int>((size_t)count * p.m_pad);
   int* eB = c.take<int>((size_t)count * p.n_pad);
-  const int splits = (count == 1) ? splitk_count(g.m, g.n, g.k) : 1;
-  double* part = c.take<double>(count == 1 ? splitk_bytes(g.m, g.n, g.k) / sizeof(double) : 0);
+  int splits = (count == 1) ? splitk_count(g.m, g.n, g.k) : 1;
+  while (splits > 1 && scratch_with_splits(g.m, g.n, g.k, slices, count, splits) > scratch_bytes) --splits;
+  double* part = c.take<double>(splits > 1 ? (size_t)splits * g.m * g.n : 0);
   View va, vb;
   va.p = g.A; va.ld = g.lda; va.rows = g.m; va.K = g.k;
   va.mode = g.a_sym_lower ? 2 : (g.ta == 'N' ? 0 : 1);
@@ -758,11 +763,9 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
                                   2.0 * slices * (double)(p.m_pad + p.n_pad) * p.k_pad), "tc_split_prep");
     dim3 blk(32, 8);
     if (p.k_pad <= 512) {
-      static bool fused_attr = false;
-      if (!fused_attr) {
-        EVD_CUDA_TRY(cudaFuncSetAttribute(k_split_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(32 * (512 + 1) * sizeof(double))));
-        fused_attr = true;
+      {
+        const evd_status_t st = ensure_dynamic_smem((const void*)k_split_fused, 32 * (512 + 1) * sizeof(double));
+        if (st != EVD_OK) return st;
       }
       const int nblk_a = (int)(p.m_pad / 32), nblk_b = (int)(p.n_pad / 32);
       k_split_fused<<<dim3((unsigned)(nblk_a + nblk_b), (unsigned)count), 256, 32 * (p.k_pad + 1) * sizeof(double),
@@ -805,12 +808,9 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
   }
   a.st = g.status ? g.status : d_dummy_status;
   const size_t smem = smem_bytes(slices);
-  static bool attr_set = false;
-  if (!attr_set) {
-    for (int q = 1; q <= OZ_MAXS; ++q)
-      EVD_CUDA_TRY(cudaFuncSetAttribute(mma_kernel(q), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem_bytes(OZ_MAXS)));
-    attr_set = true;
+  {
+    const evd_status_t st = ensure_dynamic_smem(mma_kernel(slices), smem_bytes(OZ_MAXS));
+    if (st != EVD_OK) return st;
   }
   dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)(count > 1 ? count : zsplits));
   if (grid.y > 65535) return EVD_ERR_INVALID_ARG;

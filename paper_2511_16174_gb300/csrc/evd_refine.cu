@@ -1,6 +1,7 @@
 // Ogita-Aishima eigenpair refinement (Ogita & Aishima, JJIAM 35, 2018), one or
 // more steps, with FP64-accurate residual products:
-//   R = I - X^T X,  S = X^T A X,  lam_i = s_ii / (1 - r_ii),
+//   R = I - X^T X,  S = X^T A X  (both replaced by their symmetric parts),
+//   lam_i = s_ii / (1 - r_ii),
 //   delta = 2 (||S - diag(lam)|| + ||A|| ||R||)       (Frobenius norms, which bound
 //                                                      the 2-norms from above)
 //   E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i)  if |lam_i - lam_j| > delta
@@ -63,6 +64,22 @@ __global__ void k_sum_final(const double* part, int64_t n, double* out) {
 __global__ void k_add_identity(double* R, int64_t ldr, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) R[i + i * ldr] += 1.0;
+}
+
+// R and S are symmetric by definition: replace both computed products by their
+// symmetric parts (the rounding asymmetry of S would otherwise enter E_ij + E_ji
+// divided by the eigenvalue gap).  One thread per pair (i > j).
+__global__ void k_symmetrize2(double* R, double* S, int64_t ld, int64_t n) {
+  const int64_t j = blockIdx.y;
+  for (int64_t i = j + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = 0.5 * (R[i + j * ld] + R[j + i * ld]);
+    R[i + j * ld] = r;
+    R[j + i * ld] = r;
+    const double x = 0.5 * (S[i + j * ld] + S[j + i * ld]);
+    S[i + j * ld] = x;
+    S[j + i * ld] = x;
+  }
 }
 
 __global__ void k_lambda(const double* S, const double* R, int64_t ld, int64_t n, double* lam) {
@@ -132,6 +149,7 @@ evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, doub
     g3.C = rw.S; g3.ldc = n; g3.alpha = 1.0; g3.beta = 0.0;
     st = gemm(g3, pc.ref_slices, rw.gemm_ws, rw.gemm_ws_bytes, s);
     if (st != EVD_OK) return st;
+    k_symmetrize2<<<dim3(rx, (unsigned)n), 256, 0, s>>>(rw.R, rw.S, n, n); count_launch();
     k_lambda<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(rw.S, rw.R, n, n, lam); count_launch();
     k_sumsq_partial<<<(unsigned)n, 256, 0, s>>>(rw.R, n, n, 0, nullptr, part); count_launch();
     k_sum_final<<<1, 256, 0, s>>>(part, n, norms + 1); count_launch();

@@ -360,10 +360,13 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
   const int b = pc.b;
   const int nbp = std::max(1, pc.nb / b);  // panels per block
   cudaStream_t s = pc.stream;
-  EVD_CUDA_TRY(cudaFuncSetAttribute(k_panel_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (b * b + b) * 8));
+  {
+    evd_status_t st = ensure_dynamic_smem((const void*)k_panel_qr, (size_t)(b * b + b) * 8);
+    if (st == EVD_OK) st = ensure_dynamic_smem((const void*)k_panel_qr_smem, 200 * 1024);
+    if (st != EVD_OK) return st;
+  }
   int maxG = max_coresident_blocks((const void*)k_panel_qr, PQ_NT, (b * b + b) * 8);
   if (maxG < 1) return EVD_ERR_CUDA;
-  EVD_CUDA_TRY(cudaFuncSetAttribute(k_panel_qr_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   const int maxG_smem = max_coresident_blocks((const void*)k_panel_qr_smem, PQ_NT, 200 * 1024);
   const int64_t ldz = n;  // leading dimension of VZ, ZV
   auto gemm_tag = [&](Gemm g, const char* tag, bool tc) {

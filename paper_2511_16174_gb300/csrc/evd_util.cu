@@ -1,10 +1,32 @@
 // Small device utilities: finiteness check, copies, identity.
 #include <cstdio>
+#include <map>
+#include <mutex>
 
 #include "device_util.cuh"
 #include "evd_internal.h"
 
 namespace evd {
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers
+// it: launches of other problem sizes, possibly from other threads, may still rely
+// on the larger value).
+evd_status_t ensure_dynamic_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> set;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set[func];
+  if (bytes <= cur) return EVD_OK;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+  cur = bytes;
+  return EVD_OK;
+}
+
+evd_status_t ws_fail(const char* where, size_t have, size_t need) {
+  if (getenv("EVD_DEBUG")) fprintf(stderr, "libevd: workspace too small in %s: %zu bytes, %zu needed\n", where, have, need);
+  return EVD_ERR_WORKSPACE;
+}
 
 evd_status_t cuda_fail(cudaError_t e, const char* what) {
   if (getenv("EVD_DEBUG")) fprintf(stderr, "libevd: %s failed: %s\n", what, cudaGetErrorString(e));

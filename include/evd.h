@@ -62,8 +62,10 @@ typedef enum { EVD_VALUES = 0, EVD_VECTORS = 1 } evd_job_t;
 typedef enum { EVD_FP64 = 0, EVD_SPLIT_INT8 = 1, EVD_SPLIT_BF16 = 2 } evd_prec_t;
 
 /* Create a plan for n x n problems with leading dimension lda.
- *   b   band half-width of SBR (Sec. 2.1.1; typical 32, Sec. 4.1).  0 = autotuned.
- *   nb  outer (double-blocking) width of SBR, a multiple of b.       0 = autotuned.
+ *   b   band half-width of SBR (Sec. 2.1.1; typical 32, Sec. 4.1).
+ *   nb  outer (double-blocking) width of SBR, a multiple of b.
+ *   b = nb = 0: the autotuner's cached choice (see evd_autotune), else b = 64 for
+ *   n >= 4096 and 32 below, nb = b.  b > 0, nb = 0: nb = b.
  *   stream  a cudaStream_t (passed as void*), NULL for the legacy default stream.
  * Must be called with the target device current.  Returns EVD_ERR_INVALID_ARG for
  * n < 0, lda < max(1, n), b < 0, nb < 0, b > 0 && nb % b != 0, or b > 128. */
@@ -128,10 +130,16 @@ const char* evd_status_string(evd_status_t status);
 
 /* ---------------------------------------------------------------------------
  * Batched solve: count independent symmetric problems of uneven size, each with
- * its own A (lower read, overwritten), lda, w, Q, ldq, in one captured CUDA graph
- * whose kernels are persistent and walk a longest-first work queue.  Arrays n, lda,
- * ldq are HOST arrays of length count; A, w, Q are HOST arrays of DEVICE pointers.
- * ws/ws_bytes: device workspace of at least evd_batched_workspace_size().
+ * its own A (lower read, overwritten), lda, w, Q, ldq.  Problems are assigned
+ * longest first (cost ~ n^3) to up to 8 concurrent lanes; each lane is a stream and
+ * a host thread of its own with its own part of ws.  The lanes start after the work
+ * already queued on `stream` and `stream` waits for all of them, so the call is
+ * ordered like one kernel on `stream`; it returns when every problem has been
+ * solved (it synchronizes the lanes to read each problem's status).  Arrays n,
+ * lda, ldq are HOST arrays of length count; A, w, Q are HOST arrays of DEVICE
+ * pointers.  ws/ws_bytes: device workspace of at least
+ * evd_batched_workspace_size() bytes (256-byte aligned).  Returns the first error
+ * any problem reported.
  * ------------------------------------------------------------------------- */
 evd_status_t evd_batched_workspace_size(int count, const int64_t* n_host, evd_job_t job,
                                         size_t* bytes);
@@ -175,9 +183,14 @@ evd_status_t evd_dgemm_static(char transa, char transb, int64_t m, int64_t n, in
                               int64_t ldb, double beta, double* C, int64_t ldc, int slices,
                               void* stream);
 
-/* Autotuner: time candidate (b, nb) in {32, 64, 128}^2, nb >= b, for an n x n
- * problem and cache the winner in the JSON file at cache_path (NULL = no cache).
- * Allocates its own scratch with cudaMalloc.  Returns the choice in *b, *nb. */
+/* Autotuner: time one solve of a seeded symmetric n x n matrix (after one untimed
+ * solve) for each candidate (b, nb) in {32, 64, 128}^2 with nb a multiple of b,
+ * and return the fastest in *b, *nb.  With cache_path != NULL the choice is kept
+ * per (n rounded to a power of two, job, prec) in that JSON file, and a cached
+ * entry is returned without timing.  evd_plan_create with b = nb = 0 uses the
+ * entry of the file named by the environment variable EVD_AUTOTUNE_CACHE, if
+ * there is one.  Allocates its own device memory (cudaMalloc) and runs on the
+ * legacy default stream; n <= 65535. */
 evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char* cache_path,
                           int* b, int* nb);
 

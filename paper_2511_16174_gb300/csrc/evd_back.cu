@@ -24,6 +24,7 @@
 // is therefore one batched pair of products: W_p^T = X_p^T V_p and X_p -= Y_p W_p,
 // about 2n/b waves in all instead of n^2/(2 b g) separate groups.
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 
 #include "device_util.cuh"
@@ -190,6 +191,8 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
     if (st != EVD_OK) return st;
   }
   auto kc = [&](int64_t J) { return sweep_steps_b(n, b, J * g); };
+  static const bool fused_off = getenv("EVD_BCBACK_UNFUSED") != nullptr;
+  const bool fused = !fused_off && bcback_fused_supported(pc);
   const int64_t tmax = kc(0) + nJ - 2;
   for (int64_t t = 0; t <= tmax; ++t) {
     // groups of wave t: J' = nJ - 1 - J in [jlo, jhi] with 0 <= k = t - J' < kc(J)
@@ -201,6 +204,15 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
       while (jp >= 0 && t - jp < kc(nJ - 1 - jp)) --jp;
       const int64_t jlo = jp + 1;
       const int count = (int)(jhi - jlo + 1);
+      // problem 0 (J' = jlo) is the lowest group of the run and the only one that may reach row n
+      const int64_t J0f = nJ - 1 - jlo, k0f = t - jlo;
+      const int64_t R0f = J0f * g + 1 + k0f * b;
+      if (fused) {
+        const evd_status_t st = bcback_fused_wave(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0f,
+                                                  (int)std::min<int64_t>(h, n - R0f));
+        if (st != EVD_OK) return st;
+        continue;
+      }
       if ((size_t)count * h * g > w.vg_capacity || (size_t)count * n * g > w.wt_capacity)
         return ws_fail("bc_back wave buffers", w.wt_capacity, (size_t)count * n * g);
       {

@@ -1,0 +1,582 @@
+// BC back-transformation, one wave per launch, fused (Sec. 2.1.2, blocked form).
+//
+// For the groups G_p of one wave (row-disjoint, see evd_back.cu) and X = Q:
+//     W_p^T = X_p^T V_p          (n x g, K = h rows of the group)
+//     X_p  -= Y_p W_p            (Y_p = V_p T_p)
+// with X_p = X(R0_p : R0_p + h, :), R0_p = R0_0 - p (g + b).  One CTA owns group p
+// and 128 columns c0 .. c0+127 of X and does both products on the tensor cores
+// with the split of the FP64-accurate product (evd_ozaki.cu):
+//   phase 1  D1[m][i] = sum_r X(R0+r, c0+m) V(r, i)          M = 128, N = g = 64, K = 128
+//            The CTA's converter warps read the FP64 tile of X, split it with the
+//            fixed scale 2^1 (X is orthogonal: |x| < 2) and write the slices straight
+//            into shared memory; V's slices come pre-split.
+//   exact    D1 drained into 64-bit integer sums, converted once to FP64: W^T.
+//   phase 2  D2[m][r] = sum_i W^T(m, i) Y(r, i)              M = 128, N = 128 (two
+//            halves of 64), K = g = 64.  W^T is split in the CTA (per-row scale),
+//            Y's slices come pre-split; X(R0 + r, c0 + m) -= D2[m][r].
+// Only the FP64 tile of X moves through HBM (read twice, written once):
+// no slice or W buffer is materialized in global memory.
+//
+// Roles (320 threads): warp 0 copies the pre-split blobs (bulk copies), warp 1
+// owns the tensor memory (512 columns) and issues the MMAs, warps 2..9 convert X
+// and W into slices and drain the accumulators.  Every wait is bounded.
+#include <algorithm>
+#include <cstdio>
+
+#include "device_util.cuh"
+#include "evd_internal.h"
+#include "evd_ozaki.h"
+#include "tc_common.cuh"
+
+namespace evd {
+
+namespace {
+
+using namespace tcx;
+
+constexpr int BB_G = 64;          // group size g = b
+constexpr int BB_H = 128;         // padded rows of a group (h = 2b - 1 = 127)
+constexpr int BB_THREADS = 320;
+constexpr int BB_P1_STAGES = 3;
+
+__device__ __forceinline__ int biased_exp(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+__device__ __forceinline__ int frexp_exp(int biased_max) { return (biased_max > 0) ? biased_max - 1022 : -1022; }
+
+// ---------------------------------------------------------------- prep
+// The compact WY factors of the wave's groups, with the dense products on the
+// tensor cores:
+//   k_bb_gather   V_p (128 x g, zero outside the parallelogram, rows >= h zero), tau_p
+//   product       G_p = V_p^T V_p                         (batched split product)
+//   k_bb_T        T_p upper triangular with H_0 ... H_{g-1} = I - V T V^T:
+//                 T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i)
+//   product       Y_p = V_p T_p                           (batched split product)
+//   k_bb_split    slices of V (B operand of phase 1: N = i, K = r, scale per i) and
+//                 of Y (B operand of phase 2: N = r, K = i, scale per r)
+// Problem p of wave t is the group J' = jp0 + p, J = nJ - 1 - J', k = t - J'.
+__global__ void __launch_bounds__(256) k_bb_gather(const double* __restrict__ U, const double* __restrict__ Utau,
+                                                   int64_t n, int b, int64_t nJ, int64_t t, int64_t jp0, double* Vg,
+                                                   double* taug) {
+  constexpr int g = BB_G, H = BB_H;
+  const int64_t pidx = blockIdx.x;
+  const int64_t J = nJ - 1 - (jp0 + pidx), k = t - (jp0 + pidx);
+  double* V = Vg + (size_t)pidx * H * g;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < g; i += 8) {
+    const int64_t j = J * g + i;
+    int64_t idx = -1;
+    int m = 0;
+    if (j < n - 2 && k < (n - 3 - j) / b + 1) {
+      // sweep_offset(n, b, j) + k with F(T) = sum_{s=0}^{T} floor(s / b)
+      auto F = [&](int64_t T0) -> int64_t {
+        if (T0 < 0) return 0;
+        const int64_t q = T0 / b;
+        return (int64_t)b * q * (q - 1) / 2 + q * (T0 - q * b + 1);
+      };
+      idx = F(n - 3) - F(n - 3 - j) + j + k;
+      const int64_t r0 = j + 1 + k * b;
+      m = (int)((r0 + b - 1 < n - 1) ? b : n - r0);
+    }
+    for (int r = lane; r < H; r += 32) {
+      const int q = r - i;  // reflector i occupies rows i .. i + m - 1
+      V[r + (size_t)i * H] = (idx >= 0 && q >= 0 && q < m) ? U[idx * b + q] : 0.0;
+    }
+    if (lane == 0) taug[pidx * g + i] = (idx >= 0) ? Utau[idx] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(64) k_bb_T(const double* __restrict__ Gg, const double* __restrict__ taug,
+                                             double* Tg) {
+  constexpr int g = BB_G;
+  extern __shared__ double tsm[];
+  double* G = tsm;          // g x g
+  double* T = tsm + g * g;  // g x g
+  const int q = threadIdx.x;
+  const int64_t pidx = blockIdx.x;
+  for (int idx = q; idx < g * g; idx += g) {
+    G[idx] = Gg[(size_t)pidx * g * g + idx];
+    T[idx] = 0.0;
+  }
+  __syncthreads();
+  for (int i = 0; i < g; ++i) {
+    const double ti = taug[pidx * g + i];
+    double s = 0.0;
+    if (q < i)
+      for (int l = q; l < i; ++l) s += T[q + l * g] * G[l + i * g];
+    __syncthreads();
+    if (q < i) T[q + i * g] = -ti * s;
+    if (q == i) T[q + i * g] = ti;
+    __syncthreads();
+  }
+  for (int idx = q; idx < g * g; idx += g) Tg[(size_t)pidx * g * g + idx] = T[idx];
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_bb_split(const double* __restrict__ Vg, const double* __restrict__ Yg,
+                                                  __nv_bfloat16* Vb, int* eV, __nv_bfloat16* Yb, int* eY) {
+  constexpr int g = BB_G, H = BB_H;
+  __shared__ int ex_s[H];
+  const int tid = threadIdx.x;
+  const int64_t pidx = blockIdx.x;
+  const double* V = Vg + (size_t)pidx * H * g;
+  const double* Y = Yg + (size_t)pidx * H * g;
+  const long long off = ozaki_offset(S);
+  if (tid < g) {
+    int mx = 0;
+    for (int r = 0; r < H; ++r) mx = max(mx, biased_exp(V[r + (size_t)tid * H]));
+    eV[pidx * g + tid] = frexp_exp(mx);
+    ex_s[tid] = frexp_exp(mx);
+  }
+  __syncthreads();
+  __nv_bfloat16* Vp = Vb + (size_t)pidx * S * g * H;
+  for (int u = tid; u < g * H / 8; u += 256) {
+    const int i = u / (H / 8), r0 = (u % (H / 8)) * 8;
+    long long TO[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) TO[q] = ozaki_scaled(V[(r0 + q) + (size_t)i * H], ex_s[i], S) + off;
+    for (int tt = 0; tt < S; ++tt) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        __nv_bfloat162 h2;
+        h2.x = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q], S, tt));
+        h2.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q + 1], S, tt));
+        w[q] = *reinterpret_cast<uint32_t*>(&h2);
+      }
+      *reinterpret_cast<uint4*>(Vp + blob_index(i, r0, tt, S, 64, H / 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  __syncthreads();
+  if (tid < H) {
+    int mx = 0;
+    for (int i = 0; i < g; ++i) mx = max(mx, biased_exp(Y[tid + (size_t)i * H]));
+    eY[pidx * H + tid] = frexp_exp(mx);
+    ex_s[tid] = frexp_exp(mx);
+  }
+  __syncthreads();
+  __nv_bfloat16* Yp = Yb + (size_t)pidx * S * H * g;
+  for (int u = tid; u < H * g / 8; u += 256) {
+    const int r = u / (g / 8), i0 = (u % (g / 8)) * 8;
+    long long TO[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) TO[q] = ozaki_scaled(Y[r + (size_t)(i0 + q) * H], ex_s[r], S) + off;
+    for (int tt = 0; tt < S; ++tt) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        __nv_bfloat162 h2;
+        h2.x = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q], S, tt));
+        h2.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q + 1], S, tt));
+        w[q] = *reinterpret_cast<uint32_t*>(&h2);
+      }
+      *reinterpret_cast<uint4*>(Yp + blob_index(r, i0, tt, S, 64, g / 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- fused wave
+struct WaveArgs {
+  double* X;
+  int64_t ldx, n;
+  int64_t R0;       // first row of group 0
+  int64_t gstride;  // rows between consecutive groups (g + b)
+  int h0;           // rows of group 0 (the others have h)
+  int h;            // rows of a group (2b - 1)
+  const __nv_bfloat16* Vb;
+  const int* eV;
+  const __nv_bfloat16* Yb;
+  const int* eY;
+  int* st;
+};
+
+// AND of a predicate over the 256 threads of warps 2..9 (named barrier 1).
+__device__ __forceinline__ bool bar_and_256(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)(v ? 1 : 0))
+      : "memory");
+  return r != 0;
+}
+
+// Exact 128-bit sum of one drained accumulator pair -> FP64 (scale 2^ex).
+template <int S>
+__device__ __forceinline__ double combine(long long rh, long long rl, int ex) {
+  constexpr int L = S - 1, H = (L < 3) ? L : 3, shift_hi = 7 * (L - H);
+  unsigned long long lo = (shift_hi == 0) ? (unsigned long long)rh : ((unsigned long long)rh << shift_hi);
+  long long hi = (shift_hi == 0) ? (rh >> 63) : (rh >> (64 - shift_hi));
+  if (L >= 4) {
+    const unsigned long long nlo = lo + (unsigned long long)rl;
+    hi += (rl >> 63) + (nlo < lo ? 1 : 0);
+    lo = nlo;
+  }
+  return i128_to_double(hi, lo, ex);
+}
+
+// Drain the S weight accumulators of this thread's 32 columns (TMEM lane quadrant
+// `quad`, columns half*32 .. +31 of each weight) into the two exact sums.
+template <int S>
+__device__ __forceinline__ void drain(uint32_t tmem, int quad, int half, long long* Rh, long long* Rl) {
+  constexpr int L = S - 1, H = (L < 3) ? L : 3;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) { Rh[c] = 0; Rl[c] = 0; }
+  for (int k = 0; k <= L; ++k) {
+    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + half * 32);
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      float v[16];
+      tc_ld16(taddr + 16 * hh, v);
+      if (k <= 3) {
+        const int sh = 7 * (H - k);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) Rh[16 * hh + c] += (long long)__float2int_rn(v[c]) << sh;
+      } else {
+        const int sh = 7 * (L - k);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) Rl[16 * hh + c] += (long long)__float2int_rn(v[c]) << sh;
+      }
+    }
+  }
+}
+
+// Write 8 consecutive K-values (scale e) as S slices of a K-major blob with 128-row
+// tiles: row m, K-elements k0 .. k0+7 of K-step ks; blob base for that K-step.
+template <int S>
+__device__ __forceinline__ void put8(uint8_t* blob_ks, int m, int kk0, const double* x, int e) {
+  const long long off = ozaki_offset(S);
+  long long TO[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) TO[q] = ozaki_scaled(x[q], e, S) + off;
+  const int core = ((m >> 3) * 2 + (kk0 >> 3)) * 64 + (m & 7) * 8;  // elements
+#pragma unroll
+  for (int tt = 0; tt < S; ++tt) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_bfloat162 h2;
+      h2.x = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q], S, tt));
+      h2.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q + 1], S, tt));
+      w[q] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+    *reinterpret_cast<uint4*>(blob_ks + ((size_t)tt * OZ_BM * OZ_KS + core) * 2) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2;   // one K-step of a 128-row operand (all slices)
+  constexpr uint32_t B_KS = S * OZ_BN * OZ_KS * 2;   // one K-step of a 64-row operand
+  // phase 1: A stages [0, 3 A_KS), B stages after; phase 2: W blob [0, 4 A_KS), Y half after
+  constexpr uint32_t P1_B = BB_P1_STAGES * A_KS;
+  constexpr uint32_t P2_Y = 4 * A_KS;
+  constexpr uint32_t DATA = (P1_B + BB_P1_STAGES * B_KS > P2_Y + 4 * B_KS) ? P1_B + BB_P1_STAGES * B_KS
+                                                                            : P2_Y + 4 * B_KS;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + DATA);
+  uint64_t* fullA = bars;                          // [3], 8 arrivals (converter warps)
+  uint64_t* fullB = bars + 3;                      // [3], 1 arrival + bytes
+  uint64_t* empty = bars + 6;                      // [3], MMA commit
+  uint64_t* acc1 = bars + 9;                       // phase 1 accumulators ready
+  uint64_t* fullW = bars + 10;                     // W slices written (8 arrivals)
+  uint64_t* fullY = bars + 11;                     // Y half copied (1 arrival + bytes), two phases
+  uint64_t* acc2 = bars + 12;                      // phase 2 half ready (two phases)
+  uint64_t* drained = bars + 13;                   // epilogue drained phase 2 half 0 (8 arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* eVs = reinterpret_cast<int*>(tmem_slot + 4);        // 64
+  int* eYs = eVs + BB_G;                                     // 128
+  int* exw = eYs + BB_H;                                     // 2 x 128 (per-half maxima)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = blockIdx.y;
+  const int64_t c0 = (int64_t)blockIdx.x * OZ_BM;
+  const int64_t R0 = a.R0 - p * a.gstride;
+  const int hp = (p == 0) ? a.h0 : a.h;
+  const __nv_bfloat16* Vp = a.Vb + (size_t)p * S * BB_G * BB_H;
+  const __nv_bfloat16* Yp = a.Yb + (size_t)p * S * BB_H * BB_G;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) {
+      mbar_init(smem_u32(fullA + i), 8);
+      mbar_init(smem_u32(fullB + i), 1);
+      mbar_init(smem_u32(empty + i), 1);
+    }
+    mbar_init(smem_u32(acc1), 1);
+    mbar_init(smem_u32(fullW), 8);
+    mbar_init(smem_u32(fullY), 1);
+    mbar_init(smem_u32(acc2), 1);
+    mbar_init(smem_u32(drained), 8);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < BB_G) eVs[threadIdx.x] = a.eV[p * BB_G + threadIdx.x];
+  if (threadIdx.x < BB_H) eYs[threadIdx.x] = a.eY[p * BB_H + threadIdx.x];
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- copies: V K-steps (phase 1), then the two Y halves
+      int issued = 0;
+      for (int j = 0; j < BB_H / OZ_KS; ++j) {
+        const int si = j % 3, round = j / 3;
+        if (round > 0 && !mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9101)) break;
+        mbar_expect_tx(smem_u32(fullB + si), B_KS);
+        bulk_load(smem_u32(smem + P1_B + si * B_KS), Vp + (size_t)j * S * OZ_BN * OZ_KS, B_KS, smem_u32(fullB + si));
+        ++issued;
+      }
+      if (*abort) {
+        // let the copies already in flight land before the CTA exits
+        for (int j = (issued > 3 ? issued - 3 : 0); j < issued; ++j)
+          for (long long i = 0; i < OZ_WAIT_LIMIT && !mbar_try(smem_u32(fullB + j % 3), (j / 3) & 1); ++i) {}
+      }
+      // phase 1 finished reading shared memory before the Y copy may overwrite it
+      if (!*abort && mbar_wait(smem_u32(acc1), 0, abort, a.st, 9102)) {
+        mbar_expect_tx(smem_u32(fullY), 4 * B_KS);
+        bulk_load(smem_u32(smem + P2_Y), Yp, 4 * B_KS, smem_u32(fullY));
+        // half 1 after the half-0 products have read the buffer
+        if (mbar_wait(smem_u32(acc2), 0, abort, a.st, 9103)) {
+          mbar_expect_tx(smem_u32(fullY), 4 * B_KS);
+          bulk_load(smem_u32(smem + P2_Y), Yp + (size_t)4 * S * OZ_BN * OZ_KS, 4 * B_KS, smem_u32(fullY));
+          mbar_wait(smem_u32(fullY), 1, abort, a.st, 9104);  // let the copy land before leaving
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issue
+      const uint64_t dbase = desc_kmajor(smem_u32(smem));
+      bool ok = true;
+      for (int j = 0; j < BB_H / OZ_KS && ok; ++j) {
+        const int si = j % 3, round = j / 3;
+        ok = mbar_wait(smem_u32(fullA + si), round & 1, abort, a.st, 9111) &&
+             mbar_wait(smem_u32(fullB + si), round & 1, abort, a.st, 9112);
+        if (!ok) break;
+        tc_fence_after();
+        issue_stage<S>(tmem, dbase + (uint64_t)((si * A_KS) >> 4), dbase + (uint64_t)((P1_B + si * B_KS) >> 4),
+                       j > 0 ? 1u : 0u);
+        tc_commit(smem_u32(empty + si));
+      }
+      if (ok) tc_commit(smem_u32(acc1));
+      // phase 2, half 0 then half 1 (the epilogue drains half 0 in between)
+      for (int hf = 0; hf < 2 && ok; ++hf) {
+        ok = mbar_wait(smem_u32(fullY), hf, abort, a.st, 9113);
+        if (ok && hf == 0) ok = mbar_wait(smem_u32(fullW), 0, abort, a.st, 9114);
+        if (ok && hf == 1) ok = mbar_wait(smem_u32(drained), 0, abort, a.st, 9115);
+        if (!ok) break;
+        tc_fence_after();
+        for (int ks = 0; ks < BB_G / OZ_KS; ++ks)
+          issue_stage<S>(tmem, dbase + (uint64_t)((ks * A_KS) >> 4), dbase + (uint64_t)((P2_Y + ks * B_KS) >> 4),
+                         ks > 0 ? 1u : 0u);
+        tc_commit(smem_u32(acc2));
+      }
+    }
+  } else {
+    // ---------------- converter / epilogue warps 2..9 (256 threads)
+    // Every thread of these warps passes through the same named barriers whatever
+    // happens (a bounded wait that gives up only clears `ok`), and `ok` is made
+    // uniform at each of them, so no thread can be left waiting at a barrier.
+    const int ct = threadIdx.x - 64;
+    // phase-1 producer mapping: column m = ct / 2, K half kh = ct % 2
+    const int m = ct >> 1, kh = ct & 1;
+    const int64_t col = c0 + m;
+    const bool colok = col < a.n;
+    const double* xc = a.X + col * a.ldx + R0;
+    // Scale of the X operand: X is orthogonal (the product of D&C's eigenvector
+    // matrix with orthogonal reflectors), so |x| <= 1 + O(n u) < 2 and the fixed
+    // frexp exponent 1 bounds every entry.  The split then keeps 7 S - 1 bits below
+    // 2^1: an absolute error of at most 2^(-7S) per entry (2^-56 at S = 8).
+    const int eA = 1;
+    __shared__ int eAs[BB_H];
+    if (kh == 0) eAs[m] = eA;
+    // pass over the K-steps of 16 rows, the next step's 8 values loaded ahead
+    bool ok = true;
+    double xn[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = kh * 8 + q;
+      xn[q] = (colok && r < hp) ? xc[r] : 0.0;
+    }
+    for (int j = 0; j < BB_H / OZ_KS; ++j) {
+      const int si = j % 3, round = j / 3;
+      double x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = xn[q];
+      if (j + 1 < BB_H / OZ_KS) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int r = (j + 1) * OZ_KS + kh * 8 + q;
+          xn[q] = (colok && r < hp) ? xc[r] : 0.0;
+        }
+      }
+      if (ok && round > 0) ok = mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9121);
+      if (ok) put8<S>(smem + si * A_KS, m, kh * 8, x, eA);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok && lane == 0) mbar_arrive(smem_u32(fullA + si));
+    }
+    // phase 1 result: W^T(m2, i) for this thread's TMEM lane and 32 columns
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int m2 = quad * 32 + lane;
+    if (ok) ok = mbar_wait(smem_u32(acc1), 0, abort, a.st, 9122);
+    ok = bar_and_256(ok);
+    long long Rh[32], Rl[32];
+    double wv[32];
+    int eW = 0;
+    {
+      int wmx = 0;
+      if (ok) {
+        tc_fence_after();
+        const int eAm = eAs[m2];
+        drain<S>(tmem, quad, half, Rh, Rl);
+        tc_fence_before();
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          wv[c] = combine<S>(Rh[c], Rl[c], eAm + eVs[half * 32 + c] - 14 - 7 * (S - 1));
+          wmx = max(wmx, biased_exp(wv[c]));
+        }
+      }
+      // row scale of W^T over its 64 columns (the two halves meet in shared memory)
+      exw[half * BB_H + m2] = wmx;
+      ok = bar_and_256(ok);
+      eW = frexp_exp(max(exw[m2], exw[BB_H + m2]));
+    }
+    if (ok) {
+      // W^T slices, K = i: this thread's 32 columns are K-steps 2 half and 2 half + 1
+#pragma unroll
+      for (int u = 0; u < 4; ++u) put8<S>(smem + (half * 2 + (u >> 1)) * A_KS, m2, (u & 1) * 8, wv + 8 * u, eW);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(fullW));
+    }
+    // phase 2: X(R0 + r, c0 + m2) -= D2[m2][r], r = 64 hf + 32 half + c
+    const int64_t colw = c0 + m2;
+    double* xw = a.X + colw * a.ldx + R0;
+    for (int hf = 0; hf < 2 && ok; ++hf) {
+      ok = mbar_wait(smem_u32(acc2), hf, abort, a.st, 9123);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      drain<S>(tmem, quad, half, Rh, Rl);
+      tc_fence_before();
+      __syncwarp();
+      if (hf == 0 && lane == 0) mbar_arrive(smem_u32(drained));
+      if (colw < a.n) {
+        const int rb = 64 * hf + 32 * half;
+#pragma unroll
+        for (int c0r = 0; c0r < 32; c0r += 4) {
+          double cv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cv[q] = (rb + c0r + q < hp) ? xw[rb + c0r + q] : 0.0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int r = rb + c0r + q;
+            if (r < hp) xw[r] = cv[q] - combine<S>(Rh[c0r + q], Rl[c0r + q], eW + eYs[r] - 14 - 7 * (S - 1));
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+template <int S>
+size_t wave_smem_bytes() {
+  constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2, B_KS = S * OZ_BN * OZ_KS * 2;
+  constexpr uint32_t P1 = BB_P1_STAGES * A_KS + BB_P1_STAGES * B_KS, P2 = 4 * A_KS + 4 * B_KS;
+  return 1024 + (P1 > P2 ? P1 : P2) + 14 * 8 + 16 + (BB_G + BB_H + 2 * BB_H) * 4 + 64;
+}
+
+template <int S>
+evd_status_t launch_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w, int64_t nJ,
+                         int64_t t, int64_t jlo, int count, int64_t R0, int hh0, cudaStream_t s) {
+  const int64_t n = pc.n;
+  const int b = pc.b;
+  // workspace: blobs and scales, the FP64 factors, then the products' scratch
+  Carver cv(w.gemm_ws);
+  __nv_bfloat16* Vb = cv.take<__nv_bfloat16>((size_t)count * S * BB_G * BB_H);
+  __nv_bfloat16* Yb = cv.take<__nv_bfloat16>((size_t)count * S * BB_H * BB_G);
+  int* eV = cv.take<int>((size_t)count * BB_G);
+  int* eY = cv.take<int>((size_t)count * BB_H);
+  double* Vg = cv.take<double>((size_t)count * BB_H * BB_G);
+  double* Yg = cv.take<double>((size_t)count * BB_H * BB_G);
+  double* Gg = cv.take<double>((size_t)count * BB_G * BB_G);
+  double* Tg = cv.take<double>((size_t)count * BB_G * BB_G);
+  double* taug = cv.take<double>((size_t)count * BB_G);
+  char* scratch = cv.take<char>(0);
+  const size_t used = cv.off;
+  const size_t prod = std::max(ozaki_scratch_bytes_batched(BB_G, BB_G, BB_H, pc.ref_slices, count),
+                               ozaki_scratch_bytes_batched(BB_H, BB_G, BB_G, pc.ref_slices, count));
+  if (used + prod > w.gemm_ws_bytes) return ws_fail("bc_back fused wave", w.gemm_ws_bytes, used + prod);
+  {
+    StatScope sc("bc_back_prep", s);
+    k_bb_gather<<<(unsigned)count, 256, 0, s>>>(bw.U, bw.Utau, n, b, nJ, t, jlo, Vg, taug); count_launch();
+    EVD_CUDA_TRY(cudaGetLastError());
+    // G_p = V_p^T V_p
+    Gemm gg;
+    gg.status = pc.status; gg.tag = "bc_back_prep";
+    gg.ta = 'T'; gg.m = BB_G; gg.n = BB_G; gg.k = BB_H; gg.A = Vg; gg.lda = BB_H; gg.B = Vg; gg.ldb = BB_H;
+    gg.C = Gg; gg.ldc = BB_G; gg.alpha = 1.0; gg.beta = 0.0;
+    Batch bt;
+    bt.count = count; bt.sA = (int64_t)BB_H * BB_G; bt.sB = (int64_t)BB_H * BB_G; bt.sC = (int64_t)BB_G * BB_G;
+    evd_status_t st = ozaki_gemm_batched(gg, bt, pc.ref_slices, scratch, w.gemm_ws_bytes - used, s);
+    if (st != EVD_OK) return st;
+    const size_t tsmem = 2 * (size_t)BB_G * BB_G * sizeof(double);
+    st = ensure_dynamic_smem((const void*)k_bb_T, tsmem);
+    if (st != EVD_OK) return st;
+    k_bb_T<<<(unsigned)count, BB_G, tsmem, s>>>(Gg, taug, Tg); count_launch();
+    EVD_CUDA_TRY(cudaGetLastError());
+    // Y_p = V_p T_p
+    Gemm gy;
+    gy.status = pc.status; gy.tag = "bc_back_prep";
+    gy.m = BB_H; gy.n = BB_G; gy.k = BB_G; gy.A = Vg; gy.lda = BB_H; gy.B = Tg; gy.ldb = BB_G;
+    gy.C = Yg; gy.ldc = BB_H; gy.alpha = 1.0; gy.beta = 0.0;
+    bt.sA = (int64_t)BB_H * BB_G; bt.sB = (int64_t)BB_G * BB_G; bt.sC = (int64_t)BB_H * BB_G;
+    st = ozaki_gemm_batched(gy, bt, pc.ref_slices, scratch, w.gemm_ws_bytes - used, s);
+    if (st != EVD_OK) return st;
+    k_bb_split<S><<<(unsigned)count, 256, 0, s>>>(Vg, Yg, Vb, eV, Yb, eY); count_launch();
+    EVD_CUDA_TRY(cudaGetLastError());
+  }
+  const size_t smem = wave_smem_bytes<S>();
+  evd_status_t st = ensure_dynamic_smem((const void*)k_bcback_wave<S>, smem);
+  if (st != EVD_OK) return st;
+  WaveArgs a;
+  a.X = Q; a.ldx = ldq; a.n = n; a.R0 = R0; a.gstride = 2 * b; a.h0 = hh0; a.h = 2 * b - 1;
+  a.Vb = Vb; a.eV = eV; a.Yb = Yb; a.eY = eY; a.st = pc.status;
+  dim3 grid((unsigned)ceil_div(n, OZ_BM), (unsigned)count);
+  // executed bf16 flops of the two products (tensor work of one wave)
+  const double flops = (double)count * ceil_div(n, OZ_BM) * OZ_BM * 2.0 * (BB_G * BB_H + BB_H * BB_G) *
+                       (double)(S * (S + 1) / 2);
+  StatScope sc("bc_back_wave", s, flops, (double)count * 16.0 * BB_H * (double)n, "tc_split");
+  k_bcback_wave<S><<<grid, BB_THREADS, smem, s>>>(a);
+  count_launch();
+  EVD_CUDA_TRY(cudaGetLastError());
+  return EVD_OK;
+}
+
+}  // namespace
+
+bool bcback_fused_supported(const PlanCore& pc) {
+  return pc.b == BB_G && (pc.slices == 8 || pc.slices == 6) && pc.n >= 1024;
+}
+
+evd_status_t bcback_fused_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
+                               int64_t nJ, int64_t t, int64_t jlo, int count, int64_t R0, int hh0) {
+  if (pc.slices == 8) return launch_wave<8>(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0, hh0, pc.stream);
+  return launch_wave<6>(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0, hh0, pc.stream);
+}
+
+}  // namespace evd

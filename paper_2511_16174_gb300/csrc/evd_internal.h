@@ -165,6 +165,10 @@ struct BackWork {
 };
 evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq,
                          const BackWork& w);
+// Fused BC-Back wave (b = 64, 6 or 8 slices; evd_bcback.cu).
+bool bcback_fused_supported(const PlanCore& pc);
+evd_status_t bcback_fused_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
+                               int64_t nJ, int64_t t, int64_t jlo, int count, int64_t R0, int hh0);
 evd_status_t sbr_back_run(const PlanCore& pc, const double* A, const double* sbr_T,
                           const double* sbr_tau, double* Q, int64_t ldq, const BackWork& w);
 

@@ -353,6 +353,30 @@ def ours(args):
     return 0
 
 
+def profile_target(args):
+    """A small, untimed run for ncu captures (no JSON line)."""
+    import torch
+    from paper_2511_16174_gb300 import evd, inputs
+    n = args.n
+    g = torch.Generator(device="cuda").manual_seed(inputs.SEED_BASE)
+    if args.profile == "gemm":
+        A = evd.empty_colmajor(n, n)
+        B = evd.empty_colmajor(n, n)
+        C = evd.empty_colmajor(n, n)
+        A.copy_(torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g))
+        B.copy_(torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g))
+        for _ in range(2):
+            evd.dgemm("N", "N", 1.0, A, B, 0.0, C, slices=8 if args.prec == "fp64" else 6)
+    else:
+        lam = np.sort(spectrum_for(n, inputs.SEED_BASE + 1))
+        A = evd.as_colmajor(torch.from_numpy(inputs.qlq(lam, inputs.SEED_BASE + 1)).cuda()) if n <= 8192 else \
+            evd.as_colmajor(inputs.qlq_device(lam, inputs.SEED_BASE + 1))
+        evd.syevd(A, job="V", prec=args.prec, b=args.b, nb=args.nb)
+    torch.cuda.synchronize()
+    print("profile target done", flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,7 +390,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="no per-category event timing in the timed region")
+    ap.add_argument("--profile", choices=["gemm", "solve"], default=None,
+                    help="untimed target for a profiler: one N^3 split product (N = --n) twice, or one solve")
     args = ap.parse_args()
+    if args.profile:
+        return profile_target(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

@@ -10,16 +10,18 @@
 //            The CTA's converter warps read the FP64 tile of X, split it with the
 //            fixed scale 2^1 (X is orthogonal: |x| < 2) and write the slices straight
 //            into shared memory; V's slices come pre-split.
-//   exact    D1 drained into 64-bit integer sums, converted once to FP64: W^T.
+//   exact    D1 drained into exact 128-bit integer sums (W^T times a power of two).
 //   phase 2  D2[m][r] = sum_i W^T(m, i) Y(r, i)              M = 128, N = 128 (two
-//            halves of 64), K = g = 64.  W^T is split in the CTA (per-row scale),
+//            halves of 64), K = g = 64.  W^T is split in the CTA straight from the
+//            integer sums (per-row scale, integer rescaling and rounding),
 //            Y's slices come pre-split; X(R0 + r, c0 + m) -= D2[m][r].
 // Only the FP64 tile of X moves through HBM (read twice, written once):
 // no slice or W buffer is materialized in global memory.
 //
-// Roles (320 threads): warp 0 copies the pre-split blobs (bulk copies), warp 1
-// owns the tensor memory (512 columns) and issues the MMAs, warps 2..9 convert X
-// and W into slices and drain the accumulators.  Every wait is bounded.
+// Roles (576 threads): warp 0 copies the pre-split blobs (bulk copies), warp 1
+// owns the tensor memory (512 columns) and issues the MMAs, warps 2..17 convert X
+// and W into slices and drain the accumulators (16 columns per thread).  Every
+// wait is bounded.
 #include <algorithm>
 #include <cstdio>
 
@@ -36,7 +38,7 @@ using namespace tcx;
 
 constexpr int BB_G = 64;          // group size g = b
 constexpr int BB_H = 128;         // padded rows of a group (h = 2b - 1 = 127)
-constexpr int BB_THREADS = 320;
+constexpr int BB_THREADS = 576;  // warp 0 copies, warp 1 MMA, warps 2..17 convert and drain
 constexpr int BB_P1_STAGES = 3;
 
 __device__ __forceinline__ int biased_exp(double x) {
@@ -190,77 +192,119 @@ struct WaveArgs {
   int* st;
 };
 
-// AND of a predicate over the 256 threads of warps 2..9 (named barrier 1).
-__device__ __forceinline__ bool bar_and_256(bool v) {
+// AND of a predicate over the 512 threads of warps 2..17 (named barrier 1).
+__device__ __forceinline__ bool bar_and_epi(bool v) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 512, p;\n selp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
       : "r"((uint32_t)(v ? 1 : 0))
       : "memory");
   return r != 0;
 }
 
-// Exact 128-bit sum of one drained accumulator pair -> FP64 (scale 2^ex).
+// The exact signed 128-bit value (hi, lo) of one accumulator pair:
+// R = Rh 2^(7 (L - H)) + Rl.
 template <int S>
-__device__ __forceinline__ double combine(long long rh, long long rl, int ex) {
+__device__ __forceinline__ void sum128(long long rh, long long rl, long long& hi, unsigned long long& lo) {
   constexpr int L = S - 1, H = (L < 3) ? L : 3, shift_hi = 7 * (L - H);
-  unsigned long long lo = (shift_hi == 0) ? (unsigned long long)rh : ((unsigned long long)rh << shift_hi);
-  long long hi = (shift_hi == 0) ? (rh >> 63) : (rh >> (64 - shift_hi));
+  lo = (shift_hi == 0) ? (unsigned long long)rh : ((unsigned long long)rh << shift_hi);
+  hi = (shift_hi == 0) ? (rh >> 63) : (rh >> (64 - shift_hi));
   if (L >= 4) {
     const unsigned long long nlo = lo + (unsigned long long)rl;
     hi += (rl >> 63) + (nlo < lo ? 1 : 0);
     lo = nlo;
   }
+}
+
+// FP64 value of one accumulator pair, scale 2^ex (rounded once).
+template <int S>
+__device__ __forceinline__ double combine(long long rh, long long rl, int ex) {
+  long long hi;
+  unsigned long long lo;
+  sum128<S>(rh, rl, hi, lo);
   return i128_to_double(hi, lo, ex);
 }
 
-// Drain the S weight accumulators of this thread's 32 columns (TMEM lane quadrant
-// `quad`, columns half*32 .. +31 of each weight) into the two exact sums.
+// Magnitude (uh, ul) of a signed 128-bit value, and its bit length (0 for zero).
+__device__ __forceinline__ int abs128(long long hi, unsigned long long lo, unsigned long long& uh,
+                                      unsigned long long& ul) {
+  uh = (unsigned long long)hi;
+  ul = lo;
+  if (hi < 0) {
+    ul = ~ul + 1ull;
+    uh = ~uh + (ul == 0ull ? 1ull : 0ull);
+  }
+  if (uh) return 128 - __clzll((long long)uh);
+  if (ul) return 64 - __clzll((long long)ul);
+  return 0;
+}
+
+// T = round_half_away(R 2^d) for a signed 128-bit R with |R 2^d| < 2^62.
+__device__ __forceinline__ long long scale_round(long long hi, unsigned long long lo, int d) {
+  unsigned long long uh, ul;
+  abs128(hi, lo, uh, ul);
+  unsigned long long m;
+  if (d >= 0) {
+    m = (d < 64) ? (ul << d) : 0ull;  // |R| < 2^(62 - d): the magnitude sits in the low word (R = 0 for d >= 62)
+  } else {
+    const int k = -d;
+    if (k >= 128) return 0;
+    // add half an ulp of the result, then shift right by k
+    if (k - 1 < 64) {
+      const unsigned long long add = 1ull << (k - 1);
+      const unsigned long long nl = ul + add;
+      uh += (nl < ul) ? 1ull : 0ull;
+      ul = nl;
+    } else {
+      uh += 1ull << (k - 1 - 64);
+    }
+    m = (k < 64) ? ((ul >> k) | (uh << (64 - k))) : (uh >> (k - 64));
+  }
+  return (hi < 0) ? -(long long)m : (long long)m;
+}
+
+// Drain the S weight accumulators of this thread's 16 columns (TMEM lane quadrant
+// `quad`, columns 16 q4 .. +15 of each weight) into the two exact sums.
 template <int S>
-__device__ __forceinline__ void drain(uint32_t tmem, int quad, int half, long long* Rh, long long* Rl) {
+__device__ __forceinline__ void drain16(uint32_t tmem, int quad, int q4, long long* Rh, long long* Rl) {
   constexpr int L = S - 1, H = (L < 3) ? L : 3;
 #pragma unroll
-  for (int c = 0; c < 32; ++c) { Rh[c] = 0; Rl[c] = 0; }
+  for (int c = 0; c < 16; ++c) { Rh[c] = 0; Rl[c] = 0; }
+#pragma unroll
   for (int k = 0; k <= L; ++k) {
-    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + half * 32);
+    float v[16];
+    tc_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + q4 * 16), v);
+    if (k <= 3) {
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      float v[16];
-      tc_ld16(taddr + 16 * hh, v);
-      if (k <= 3) {
-        const int sh = 7 * (H - k);
+      for (int c = 0; c < 16; ++c) Rh[c] += (long long)__float2int_rn(v[c]) << (7 * (H - k));
+    } else {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) Rh[16 * hh + c] += (long long)__float2int_rn(v[c]) << sh;
-      } else {
-        const int sh = 7 * (L - k);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) Rl[16 * hh + c] += (long long)__float2int_rn(v[c]) << sh;
-      }
+      for (int c = 0; c < 16; ++c) Rl[c] += (long long)__float2int_rn(v[c]) << (7 * (L - k));
     }
   }
 }
 
-// Write 8 consecutive K-values (scale e) as S slices of a K-major blob with 128-row
-// tiles: row m, K-elements k0 .. k0+7 of K-step ks; blob base for that K-step.
-template <int S>
-__device__ __forceinline__ void put8(uint8_t* blob_ks, int m, int kk0, const double* x, int e) {
+// Write the S digit slices of n consecutive K-values (already scaled integers T,
+// n = 4 or 8, kk0 a multiple of n) into a K-major blob with 128-row tiles: row m,
+// K-elements kk0 .. kk0+n-1 of the blob's K-step.
+template <int S, int NV>
+__device__ __forceinline__ void put_digits(uint8_t* blob_ks, int m, int kk0, const long long* T) {
   const long long off = ozaki_offset(S);
-  long long TO[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) TO[q] = ozaki_scaled(x[q], e, S) + off;
-  const int core = ((m >> 3) * 2 + (kk0 >> 3)) * 64 + (m & 7) * 8;  // elements
+  const int core = ((m >> 3) * 2 + (kk0 >> 3)) * 64 + (m & 7) * 8 + (kk0 & 7);  // elements
 #pragma unroll
   for (int tt = 0; tt < S; ++tt) {
-    uint32_t w[4];
+    uint32_t w[NV / 2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < NV / 2; ++q) {
       __nv_bfloat162 h2;
-      h2.x = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q], S, tt));
-      h2.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q + 1], S, tt));
+      h2.x = __float2bfloat16_rn((float)ozaki_digit(T[2 * q] + off, S, tt));
+      h2.y = __float2bfloat16_rn((float)ozaki_digit(T[2 * q + 1] + off, S, tt));
       w[q] = *reinterpret_cast<uint32_t*>(&h2);
     }
-    *reinterpret_cast<uint4*>(blob_ks + ((size_t)tt * OZ_BM * OZ_KS + core) * 2) = make_uint4(w[0], w[1], w[2], w[3]);
+    uint8_t* dst = blob_ks + ((size_t)tt * OZ_BM * OZ_KS + core) * 2;
+    if (NV == 8) *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2 % (NV / 2)], w[3 % (NV / 2)]);
+    else *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
   }
 }
 
@@ -276,19 +320,19 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
   constexpr uint32_t DATA = (P1_B + BB_P1_STAGES * B_KS > P2_Y + 4 * B_KS) ? P1_B + BB_P1_STAGES * B_KS
                                                                             : P2_Y + 4 * B_KS;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + DATA);
-  uint64_t* fullA = bars;                          // [3], 8 arrivals (converter warps)
+  uint64_t* fullA = bars;                          // [3], 16 arrivals (converter warps)
   uint64_t* fullB = bars + 3;                      // [3], 1 arrival + bytes
   uint64_t* empty = bars + 6;                      // [3], MMA commit
   uint64_t* acc1 = bars + 9;                       // phase 1 accumulators ready
-  uint64_t* fullW = bars + 10;                     // W slices written (8 arrivals)
+  uint64_t* fullW = bars + 10;                     // W slices written (16 arrivals)
   uint64_t* fullY = bars + 11;                     // Y half copied (1 arrival + bytes), two phases
   uint64_t* acc2 = bars + 12;                      // phase 2 half ready (two phases)
-  uint64_t* drained = bars + 13;                   // epilogue drained phase 2 half 0 (8 arrivals)
+  uint64_t* drained = bars + 13;                   // epilogue drained phase 2 half 0 (16 arrivals)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* eVs = reinterpret_cast<int*>(tmem_slot + 4);        // 64
   int* eYs = eVs + BB_G;                                     // 128
-  int* exw = eYs + BB_H;                                     // 2 x 128 (per-half maxima)
+  int* exw = eYs + BB_H;                                     // 4 x 128 (per-quarter maxima)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = blockIdx.y;
   const int64_t c0 = (int64_t)blockIdx.x * OZ_BM;
@@ -299,15 +343,15 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 3; ++i) {
-      mbar_init(smem_u32(fullA + i), 8);
+      mbar_init(smem_u32(fullA + i), 16);
       mbar_init(smem_u32(fullB + i), 1);
       mbar_init(smem_u32(empty + i), 1);
     }
     mbar_init(smem_u32(acc1), 1);
-    mbar_init(smem_u32(fullW), 8);
+    mbar_init(smem_u32(fullW), 16);
     mbar_init(smem_u32(fullY), 1);
     mbar_init(smem_u32(acc2), 1);
-    mbar_init(smem_u32(drained), 8);
+    mbar_init(smem_u32(drained), 16);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -380,13 +424,13 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
       }
     }
   } else {
-    // ---------------- converter / epilogue warps 2..9 (256 threads)
+    // ---------------- converter / epilogue warps 2..17 (512 threads)
     // Every thread of these warps passes through the same named barriers whatever
     // happens (a bounded wait that gives up only clears `ok`), and `ok` is made
     // uniform at each of them, so no thread can be left waiting at a barrier.
     const int ct = threadIdx.x - 64;
-    // phase-1 producer mapping: column m = ct / 2, K half kh = ct % 2
-    const int m = ct >> 1, kh = ct & 1;
+    // phase 1 producer mapping: column m = ct / 4, rows 4 kq .. 4 kq + 3 of a K-step
+    const int m = ct >> 2, kq = ct & 3;
     const int64_t col = c0 + m;
     const bool colok = col < a.n;
     const double* xc = a.X + col * a.ldx + R0;
@@ -394,90 +438,101 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
     // matrix with orthogonal reflectors), so |x| <= 1 + O(n u) < 2 and the fixed
     // frexp exponent 1 bounds every entry.  The split then keeps 7 S - 1 bits below
     // 2^1: an absolute error of at most 2^(-7S) per entry (2^-56 at S = 8).
-    const int eA = 1;
-    __shared__ int eAs[BB_H];
-    if (kh == 0) eAs[m] = eA;
-    // pass over the K-steps of 16 rows, the next step's 8 values loaded ahead
+    constexpr int eA = 1;
     bool ok = true;
-    double xn[8];
+    double xn[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int r = kh * 8 + q;
+    for (int q = 0; q < 4; ++q) {
+      const int r = kq * 4 + q;
       xn[q] = (colok && r < hp) ? xc[r] : 0.0;
     }
     for (int j = 0; j < BB_H / OZ_KS; ++j) {
       const int si = j % 3, round = j / 3;
-      double x[8];
+      long long T[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) x[q] = xn[q];
-      if (j + 1 < BB_H / OZ_KS) {
+      for (int q = 0; q < 4; ++q) T[q] = ozaki_scaled(xn[q], eA, S);
+      if (j + 1 < BB_H / OZ_KS) {  // the next K-step's values, loaded ahead
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int r = (j + 1) * OZ_KS + kh * 8 + q;
+        for (int q = 0; q < 4; ++q) {
+          const int r = (j + 1) * OZ_KS + kq * 4 + q;
           xn[q] = (colok && r < hp) ? xc[r] : 0.0;
         }
       }
       if (ok && round > 0) ok = mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9121);
-      if (ok) put8<S>(smem + si * A_KS, m, kh * 8, x, eA);
+      if (ok) put_digits<S, 4>(smem + si * A_KS, m, kq * 4, T);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       ok = __all_sync(0xffffffffu, ok);
       if (ok && lane == 0) mbar_arrive(smem_u32(fullA + si));
     }
-    // phase 1 result: W^T(m2, i) for this thread's TMEM lane and 32 columns
-    const int quad = warp & 3, half = (warp - 2) >> 2;
+    // phase 1 result: W^T(m2, i), i = 16 q4 .. +15, as exact 128-bit integers
+    const int quad = warp & 3, q4 = (warp - 2) >> 2;
     const int m2 = quad * 32 + lane;
     if (ok) ok = mbar_wait(smem_u32(acc1), 0, abort, a.st, 9122);
-    ok = bar_and_256(ok);
-    long long Rh[32], Rl[32];
-    double wv[32];
-    int eW = 0;
+    ok = bar_and_epi(ok);
+    long long Rh[16], Rl[16];
+    int eW = -1022;
     {
-      int wmx = 0;
+      int bmax = -100000;  // max over this thread's columns of bitlen(R) + scale
       if (ok) {
         tc_fence_after();
-        const int eAm = eAs[m2];
-        drain<S>(tmem, quad, half, Rh, Rl);
+        drain16<S>(tmem, quad, q4, Rh, Rl);
         tc_fence_before();
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          wv[c] = combine<S>(Rh[c], Rl[c], eAm + eVs[half * 32 + c] - 14 - 7 * (S - 1));
-          wmx = max(wmx, biased_exp(wv[c]));
+        for (int c = 0; c < 16; ++c) {
+          long long hi;
+          unsigned long long lo, uh, ul;
+          sum128<S>(Rh[c], Rl[c], hi, lo);
+          const int bl = abs128(hi, lo, uh, ul);
+          if (bl > 0) bmax = max(bmax, bl + eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1));
         }
       }
-      // row scale of W^T over its 64 columns (the two halves meet in shared memory)
-      exw[half * BB_H + m2] = wmx;
-      ok = bar_and_256(ok);
-      eW = frexp_exp(max(exw[m2], exw[BB_H + m2]));
+      // row scale of W^T over its 64 columns (the four quarters meet in shared memory)
+      exw[q4 * BB_H + m2] = bmax;
+      ok = bar_and_epi(ok);
+      const int e4 = max(max(exw[m2], exw[BB_H + m2]), max(exw[2 * BB_H + m2], exw[3 * BB_H + m2]));
+      eW = (e4 > -100000) ? e4 : -1022;
     }
     if (ok) {
-      // W^T slices, K = i: this thread's 32 columns are K-steps 2 half and 2 half + 1
+      // W^T slices, K = i: this thread's 16 columns are K-step q4 (integer rescaling
+      // of the exact sums, no FP64 round trip)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) put8<S>(smem + (half * 2 + (u >> 1)) * A_KS, m2, (u & 1) * 8, wv + 8 * u, eW);
+      for (int u = 0; u < 2; ++u) {
+        long long T[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = 8 * u + q;
+          long long hi;
+          unsigned long long lo;
+          sum128<S>(Rh[c], Rl[c], hi, lo);
+          T[q] = scale_round(hi, lo, eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1) + 7 * S - eW);
+        }
+        put_digits<S, 8>(smem + q4 * A_KS, m2, 8 * u, T);
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(fullW));
     }
-    // phase 2: X(R0 + r, c0 + m2) -= D2[m2][r], r = 64 hf + 32 half + c
+    // phase 2: X(R0 + r, c0 + m2) -= D2[m2][r], r = 64 hf + 16 q4 + c
     const int64_t colw = c0 + m2;
     double* xw = a.X + colw * a.ldx + R0;
     for (int hf = 0; hf < 2 && ok; ++hf) {
+      const int rb = 64 * hf + 16 * q4;
       ok = mbar_wait(smem_u32(acc2), hf, abort, a.st, 9123);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
-      drain<S>(tmem, quad, half, Rh, Rl);
+      drain16<S>(tmem, quad, q4, Rh, Rl);
       tc_fence_before();
       __syncwarp();
       if (hf == 0 && lane == 0) mbar_arrive(smem_u32(drained));
       if (colw < a.n) {
-        const int rb = 64 * hf + 32 * half;
 #pragma unroll
-        for (int c0r = 0; c0r < 32; c0r += 4) {
-          double cv[4];
+        for (int c0r = 0; c0r < 16; c0r += 8) {
+          double cv[8];  // the 8 loads go out before any store
 #pragma unroll
-          for (int q = 0; q < 4; ++q) cv[q] = (rb + c0r + q < hp) ? xw[rb + c0r + q] : 0.0;
+          for (int q = 0; q < 8; ++q) cv[q] = (rb + c0r + q < hp) ? xw[rb + c0r + q] : 0.0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < 8; ++q) {
             const int r = rb + c0r + q;
             if (r < hp) xw[r] = cv[q] - combine<S>(Rh[c0r + q], Rl[c0r + q], eW + eYs[r] - 14 - 7 * (S - 1));
           }
@@ -497,7 +552,7 @@ template <int S>
 size_t wave_smem_bytes() {
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2, B_KS = S * OZ_BN * OZ_KS * 2;
   constexpr uint32_t P1 = BB_P1_STAGES * A_KS + BB_P1_STAGES * B_KS, P2 = 4 * A_KS + 4 * B_KS;
-  return 1024 + (P1 > P2 ? P1 : P2) + 14 * 8 + 16 + (BB_G + BB_H + 2 * BB_H) * 4 + 64;
+  return 1024 + (P1 > P2 ? P1 : P2) + 14 * 8 + 16 + (BB_G + BB_H + 4 * BB_H) * 4 + 64;
 }
 
 template <int S>

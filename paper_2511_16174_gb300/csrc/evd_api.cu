@@ -76,9 +76,12 @@ size_t dc_union_bytes(int64_t n) {
 }
 size_t back_union_bytes(int64_t n, int b) {
   Carver c(nullptr);
-  c.take<double>((size_t)n * b);
-  c.take<double>((size_t)n * b);
-  c.take<double>((size_t)n * b);
+  const int64_t K = (int64_t)kSbrBackPanels * b;
+  c.take<double>((size_t)n * K);
+  c.take<double>((size_t)n * K);
+  c.take<double>((size_t)n * K);
+  c.take<double>((size_t)K * K);
+  c.take<double>((size_t)2 * K * b);
   const int64_t pmax = bc_wave_max_groups(n, b), h = 2 * b - 1;
   c.take<double>((size_t)pmax * h * b);
   c.take<double>((size_t)pmax * h * b);
@@ -177,9 +180,12 @@ BackWork back_work(const evd_plan_s* p, const WsLayout& L) {
   Carver c(L.uni);
   BackWork w;
   w.Tg = nullptr;
-  w.Vp = c.take<double>((size_t)n * b);
-  w.Wp = c.take<double>((size_t)n * b);
-  w.Tp = c.take<double>((size_t)n * b);
+  const int64_t K = (int64_t)kSbrBackPanels * b;
+  w.Vp = c.take<double>((size_t)n * K);
+  w.Wp = c.take<double>((size_t)n * K);
+  w.Tp = c.take<double>((size_t)n * K);
+  w.Tblk = c.take<double>((size_t)K * K);
+  w.Cblk = c.take<double>((size_t)2 * K * b);
   const int64_t pmax = bc_wave_max_groups(n, b), h = 2 * b - 1;
   w.Vg = c.take<double>((size_t)pmax * h * b);
   w.Yg = c.take<double>((size_t)pmax * h * b);

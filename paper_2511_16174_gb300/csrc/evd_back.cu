@@ -154,13 +154,16 @@ __global__ void __launch_bounds__(256) k_bcback_prep(const double* __restrict__ 
   }
 }
 
-// Explicit V of SBR panel p: V(r, i) = 0 (r < i), 1 (r == i), A(r0 + r, c0 + i) (r > i).
-__global__ void k_explicit_v(const double* A, int64_t lda, int64_t r0, int64_t c0, int64_t m, int kb, double* V,
-                             int64_t ldv) {
+// Explicit V of SBR panel p inside a block of panels: rows [0, roff) of the block
+// are zero, and below them V(r, i) = 0 (r < i), 1 (r == i), A(r0 + r, c0 + i)
+// (r > i) with r counted from roff.  m = rows of the block.
+__global__ void k_explicit_v(const double* A, int64_t lda, int64_t r0, int64_t c0, int64_t roff, int64_t m, int kb,
+                             double* V, int64_t ldv) {
   const int i = blockIdx.y;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < m; rr += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = rr - roff;
     double x = (r < i) ? 0.0 : (r == i ? 1.0 : A[(r0 + r) + (c0 + i) * lda]);
-    V[r + (int64_t)i * ldv] = x;
+    V[rr + (int64_t)i * ldv] = x;
   }
 }
 
@@ -251,42 +254,89 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   return EVD_OK;
 }
 
+// SBR-Back, blocked: Q_s = H_0 H_1 ... H_{np-1} with H_p = I - V_p T_p V_p^T.  Groups
+// of kSbrBackPanels consecutive panels are merged into one compact WY form
+// H_{p0} ... H_{p1} = I - V T V^T, V = [V_{p0} .. V_{p1}] (panel p's reflectors start
+// (p - p0) b rows below the block's first row) and, panel by panel,
+//     T = [[T_prev, -T_prev (V_prev^T V_p) T_p], [0, T_p]],
+// so that X <- (I - V T V^T) X streams X once per group instead of once per panel.
+// Groups are applied last group first, as the panels are.
 evd_status_t sbr_back_run(const PlanCore& pc, const double* A, const double* sbr_T, const double* sbr_tau,
                           double* Q, int64_t ldq, const BackWork& w) {
   (void)sbr_tau;
   const int64_t n = pc.n, lda = pc.lda;
   const int b = pc.b;
+  const int qmax = kSbrBackPanels;
+  const int64_t ldk = (int64_t)qmax * b;  // leading dimension of the Kb x n buffers and of T_blk
   cudaStream_t s = pc.stream;
-  // number of factored panels
-  int64_t np = 0;
+  int64_t np = 0;  // number of factored panels
   while (n - (np * b + b) >= 2) ++np;
-  for (int64_t p = np - 1; p >= 0; --p) {
-    const int64_t c0 = p * b, r0 = c0 + b, m = n - r0;
-    const int bw = (int)((n - c0 < b) ? n - c0 : b);
-    const int kb = (int)((bw < m) ? bw : m);
-    k_explicit_v<<<dim3((unsigned)std::min<int64_t>(ceil_div(m, 256), 64), (unsigned)kb), 256, 0, s>>>(
-        A, lda, r0, c0, m, kb, w.Vp, n); count_launch();
+  auto pgemm = [&](Gemm g, int slices) {
+    g.status = pc.status;
+    g.tag = "sbr_back";
+    return gemm(g, slices, w.gemm_ws, w.gemm_ws_bytes, s);
+  };
+  for (int64_t p1 = np - 1; p1 >= 0; p1 -= qmax) {
+    const int64_t p0 = std::max<int64_t>(0, p1 - qmax + 1);
+    const int64_t R = p0 * b + b, M = n - R;  // rows of the block
+    // explicit V of the block, and the width of each panel
+    int kbs[kSbrBackPanels];
+    int64_t Kb = 0;
+    for (int64_t p = p0; p <= p1; ++p) {
+      const int64_t c0 = p * b, r0 = c0 + b, m = n - r0;
+      const int bw = (int)((n - c0 < b) ? n - c0 : b);
+      const int kb = (int)((bw < m) ? bw : m);
+      kbs[p - p0] = kb;
+      k_explicit_v<<<dim3((unsigned)std::min<int64_t>(ceil_div(M, 256), 64), (unsigned)kb), 256, 0, s>>>(
+          A, lda, r0, c0, (p - p0) * b, M, kb, w.Vp + Kb * n, n); count_launch();
+      Kb += kb;
+    }
     EVD_CUDA_TRY(cudaGetLastError());
-    // Wp = V^T X(r0:, :)   (kb x n)
+    // T of the block (Kb x Kb, upper triangular, ld ldk)
+    EVD_CUDA_TRY(cudaMemset2DAsync(w.Tblk, ldk * sizeof(double), 0, Kb * sizeof(double), Kb, s));
+    int64_t Kp = 0;
+    for (int64_t p = p0; p <= p1; ++p) {
+      const int kb = kbs[p - p0];
+      EVD_CUDA_TRY(cudaMemcpy2DAsync(w.Tblk + Kp + Kp * ldk, ldk * sizeof(double), sbr_T + (size_t)p * b * b,
+                                     b * sizeof(double), kb * sizeof(double), kb, cudaMemcpyDeviceToDevice, s));
+      if (Kp > 0) {
+        // C = V_prev^T V_p   (Kp x kb, K = M)
+        Gemm gc;
+        gc.ta = 'T'; gc.m = Kp; gc.n = kb; gc.k = M; gc.A = w.Vp; gc.lda = n; gc.B = w.Vp + Kp * n; gc.ldb = n;
+        gc.C = w.Cblk; gc.ldc = ldk; gc.alpha = 1.0; gc.beta = 0.0;
+        evd_status_t st = pgemm(gc, pc.slices);
+        if (st != EVD_OK) return st;
+        // D = T_prev C, then T(0:Kp, Kp:Kp+kb) = -D T_p
+        Gemm gd;
+        gd.m = Kp; gd.n = kb; gd.k = Kp; gd.A = w.Tblk; gd.lda = ldk; gd.B = w.Cblk; gd.ldb = ldk;
+        gd.C = w.Cblk + (size_t)ldk * b; gd.ldc = ldk; gd.alpha = 1.0; gd.beta = 0.0;
+        st = pgemm(gd, 0);
+        if (st != EVD_OK) return st;
+        Gemm ge;
+        ge.m = Kp; ge.n = kb; ge.k = kb; ge.A = gd.C; ge.lda = ldk; ge.B = w.Tblk + Kp + Kp * ldk; ge.ldb = ldk;
+        ge.C = w.Tblk + Kp * ldk; ge.ldc = ldk; ge.alpha = -1.0; ge.beta = 0.0;
+        st = pgemm(ge, 0);
+        if (st != EVD_OK) return st;
+      }
+      Kp += kb;
+    }
+    // W = V^T X(R:, :)   (Kb x n)
     Gemm g1;
-    g1.status = pc.status;
-    g1.ta = 'T'; g1.m = kb; g1.n = n; g1.k = m; g1.A = w.Vp; g1.lda = n; g1.B = Q + r0; g1.ldb = ldq;
-    g1.C = w.Wp; g1.ldc = b; g1.alpha = 1.0; g1.beta = 0.0;
-    evd_status_t st = gemm(g1, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
+    g1.ta = 'T'; g1.m = Kb; g1.n = n; g1.k = M; g1.A = w.Vp; g1.lda = n; g1.B = Q + R; g1.ldb = ldq;
+    g1.C = w.Wp; g1.ldc = ldk; g1.alpha = 1.0; g1.beta = 0.0;
+    evd_status_t st = pgemm(g1, pc.slices);
     if (st != EVD_OK) return st;
-    // Tp = T Wp  (kb x n), T upper triangular kb x kb (ld b)
+    // Tp = T W  (Kb x n)
     Gemm g2;
-    g2.status = pc.status;
-    g2.m = kb; g2.n = n; g2.k = kb; g2.A = sbr_T + (size_t)p * b * b; g2.lda = b; g2.B = w.Wp; g2.ldb = b;
-    g2.C = w.Tp; g2.ldc = b; g2.alpha = 1.0; g2.beta = 0.0;
-    st = gemm(g2, 0, nullptr, 0, s);
+    g2.m = Kb; g2.n = n; g2.k = Kb; g2.A = w.Tblk; g2.lda = ldk; g2.B = w.Wp; g2.ldb = ldk;
+    g2.C = w.Tp; g2.ldc = ldk; g2.alpha = 1.0; g2.beta = 0.0;
+    st = pgemm(g2, pc.slices);
     if (st != EVD_OK) return st;
-    // X(r0:, :) -= V Tp
+    // X(R:, :) -= V Tp
     Gemm g3;
-    g3.status = pc.status;
-    g3.m = m; g3.n = n; g3.k = kb; g3.A = w.Vp; g3.lda = n; g3.B = w.Tp; g3.ldb = b;
-    g3.C = Q + r0; g3.ldc = ldq; g3.alpha = -1.0; g3.beta = 1.0;
-    st = gemm(g3, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
+    g3.m = M; g3.n = n; g3.k = Kb; g3.A = w.Vp; g3.lda = n; g3.B = w.Tp; g3.ldb = ldk;
+    g3.C = Q + R; g3.ldc = ldq; g3.alpha = -1.0; g3.beta = 1.0;
+    st = pgemm(g3, pc.slices);
     if (st != EVD_OK) return st;
   }
   return EVD_OK;

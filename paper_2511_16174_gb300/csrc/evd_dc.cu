@@ -570,6 +570,7 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
         const MergeDesc& M = all[b0 + q];
         const int64_t m = M.n1 + M.n2, off = M.off;
         Gemm g;
+        g.tag = "dc_merge_gemm";
         g.status = pc.status;
         g.m = m; g.n = k; g.k = k;
         g.A = w.Qn + off + off * n; g.lda = n;

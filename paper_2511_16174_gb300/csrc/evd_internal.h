@@ -150,6 +150,7 @@ struct DcWork {
 evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t ldq,
                     const DcWork& w);
 
+constexpr int kSbrBackPanels = 4;  // SBR panels merged into one compact WY group in SBR-Back
 struct BackWork {
   double* Tg;      // T factors of the BC reflector groups
   double* Vg;      // V of the BC reflector groups of one wave (count x h x g)
@@ -157,9 +158,11 @@ struct BackWork {
   double* Wt;      // W^T of the same groups (count x n x g)
   size_t vg_capacity = 0;  // doubles available in Vg (and in Yg)
   size_t wt_capacity = 0;  // doubles available in Wt
-  double* Vp;      // explicit V of an SBR panel block (n x nb)
-  double* Wp;      // nb x n
-  double* Tp;      // nb x nb
+  double* Vp;      // explicit V of a group of SBR panels (n x kSbrBackPanels b)
+  double* Wp;      // kSbrBackPanels b x n
+  double* Tp;      // kSbrBackPanels b x n
+  double* Tblk;    // T of the group, (kSbrBackPanels b)^2
+  double* Cblk;    // cross products V_prev^T V_p and T_prev C, 2 x (kSbrBackPanels b) x bb
   void* gemm_ws;
   size_t gemm_ws_bytes;
 };

@@ -196,6 +196,10 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   auto kc = [&](int64_t J) { return sweep_steps_b(n, b, J * g); };
   static const bool fused_off = getenv("EVD_BCBACK_UNFUSED") != nullptr;
   const bool fused = !fused_off && bcback_fused_supported(pc);
+  if (fused) {
+    const evd_status_t st = bcback_fixed_point(pc, Q, ldq, true);
+    if (st != EVD_OK) return st;
+  }
   const int64_t tmax = kc(0) + nJ - 2;
   for (int64_t t = 0; t <= tmax; ++t) {
     // groups of wave t: J' = nJ - 1 - J in [jlo, jhi] with 0 <= k = t - J' < kc(J)
@@ -251,6 +255,7 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
       if (st != EVD_OK) return st;
     }
   }
+  if (fused) return bcback_fixed_point(pc, Q, ldq, false);
   return EVD_OK;
 }
 

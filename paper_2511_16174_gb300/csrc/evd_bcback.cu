@@ -7,16 +7,21 @@
 // and 128 columns c0 .. c0+127 of X and does both products on the tensor cores
 // with the split of the FP64-accurate product (evd_ozaki.cu):
 //   phase 1  D1[m][i] = sum_r X(R0+r, c0+m) V(r, i)          M = 128, N = g = 64, K = 128
-//            The CTA's converter warps read the FP64 tile of X, split it with the
-//            fixed scale 2^1 (X is orthogonal: |x| < 2) and write the slices straight
-//            into shared memory; V's slices come pre-split.
+//            The CTA's converter warps read the fixed-point tile of X, write its
+//            digits straight into shared memory; V's slices come pre-split.
 //   exact    D1 drained into exact 128-bit integer sums (W^T times a power of two).
 //   phase 2  D2[m][r] = sum_i W^T(m, i) Y(r, i)              M = 128, N = 128 (two
 //            halves of 64), K = g = 64.  W^T is split in the CTA straight from the
 //            integer sums (per-row scale, integer rescaling and rounding),
 //            Y's slices come pre-split; X(R0 + r, c0 + m) -= D2[m][r].
-// Only the FP64 tile of X moves through HBM (read twice, written once):
-// no slice or W buffer is materialized in global memory.
+// X is kept in fixed point during BC-Back: T = round(x 2^(7S - 1)) in int64, in
+// place of the FP64 values (bcback_fixed_point converts on entry and exit).  X is
+// orthogonal (D&C's eigenvectors times orthogonal reflectors), so |x| < 2 and
+// |T| < 2^(7S).  The split of the X operand is then the integer itself and each
+// update is an exact 128-bit rescale and one int64 subtraction; every update rounds
+// once to the grid 2^(1-7S) (at most 2^-56 at S = 8, far below FP64's
+// product error over the 2n/b waves).  Only the int64 tile of X moves through HBM
+// (read twice, written once): no slice or W buffer is materialized in global memory.
 //
 // Roles (576 threads): warp 0 copies the pre-split blobs (bulk copies), warp 1
 // owns the tensor memory (512 columns) and issues the MMAs, warps 2..17 convert X
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(256) k_bb_split(const double* __restrict__ Vg,
 
 // ---------------------------------------------------------------- fused wave
 struct WaveArgs {
-  double* X;
+  long long* X;     // X in fixed point: x = T 2^(1 - 7S) (see bcback_fixed_point)
   int64_t ldx, n;
   int64_t R0;       // first row of group 0
   int64_t gstride;  // rows between consecutive groups (g + b)
@@ -215,15 +220,6 @@ __device__ __forceinline__ void sum128(long long rh, long long rl, long long& hi
     hi += (rl >> 63) + (nlo < lo ? 1 : 0);
     lo = nlo;
   }
-}
-
-// FP64 value of one accumulator pair, scale 2^ex (rounded once).
-template <int S>
-__device__ __forceinline__ double combine(long long rh, long long rl, int ex) {
-  long long hi;
-  unsigned long long lo;
-  sum128<S>(rh, rl, hi, lo);
-  return i128_to_double(hi, lo, ex);
 }
 
 // Magnitude (uh, ul) of a signed 128-bit value, and its bit length (0 for zero).
@@ -433,29 +429,28 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
     const int m = ct >> 2, kq = ct & 3;
     const int64_t col = c0 + m;
     const bool colok = col < a.n;
-    const double* xc = a.X + col * a.ldx + R0;
-    // Scale of the X operand: X is orthogonal (the product of D&C's eigenvector
-    // matrix with orthogonal reflectors), so |x| <= 1 + O(n u) < 2 and the fixed
-    // frexp exponent 1 bounds every entry.  The split then keeps 7 S - 1 bits below
-    // 2^1: an absolute error of at most 2^(-7S) per entry (2^-56 at S = 8).
+    const long long* xc = a.X + col * a.ldx + R0;
+    // X is held in fixed point on the grid 2^(1 - 7S): the split of the X operand
+    // with the fixed scale 2^1 is then the integer itself (X is orthogonal, so
+    // |x| < 2 and |T| < 2^(7S)).
     constexpr int eA = 1;
     bool ok = true;
-    double xn[4];
+    long long xn[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = kq * 4 + q;
-      xn[q] = (colok && r < hp) ? xc[r] : 0.0;
+      xn[q] = (colok && r < hp) ? xc[r] : 0ll;
     }
     for (int j = 0; j < BB_H / OZ_KS; ++j) {
       const int si = j % 3, round = j / 3;
       long long T[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) T[q] = ozaki_scaled(xn[q], eA, S);
+      for (int q = 0; q < 4; ++q) T[q] = xn[q];
       if (j + 1 < BB_H / OZ_KS) {  // the next K-step's values, loaded ahead
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int r = (j + 1) * OZ_KS + kq * 4 + q;
-          xn[q] = (colok && r < hp) ? xc[r] : 0.0;
+          xn[q] = (colok && r < hp) ? xc[r] : 0ll;
         }
       }
       if (ok && round > 0) ok = mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9121);
@@ -514,7 +509,7 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
     }
     // phase 2: X(R0 + r, c0 + m2) -= D2[m2][r], r = 64 hf + 16 q4 + c
     const int64_t colw = c0 + m2;
-    double* xw = a.X + colw * a.ldx + R0;
+    long long* xw = a.X + colw * a.ldx + R0;
     for (int hf = 0; hf < 2 && ok; ++hf) {
       const int rb = 64 * hf + 16 * q4;
       ok = mbar_wait(smem_u32(acc2), hf, abort, a.st, 9123);
@@ -528,13 +523,19 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
       if (colw < a.n) {
 #pragma unroll
         for (int c0r = 0; c0r < 16; c0r += 8) {
-          double cv[8];  // the 8 loads go out before any store
+          long long cv[8];  // the 8 loads go out before any store
 #pragma unroll
-          for (int q = 0; q < 8; ++q) cv[q] = (rb + c0r + q < hp) ? xw[rb + c0r + q] : 0.0;
+          for (int q = 0; q < 8; ++q) cv[q] = (rb + c0r + q < hp) ? xw[rb + c0r + q] : 0ll;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int r = rb + c0r + q;
-            if (r < hp) xw[r] = cv[q] - combine<S>(Rh[c0r + q], Rl[c0r + q], eW + eYs[r] - 14 - 7 * (S - 1));
+            if (r < hp) {
+              // delta = R 2^(eW + eY_r - 14 - 7L) on the grid 2^(1 - 7S), rounded once
+              long long hi;
+              unsigned long long lo;
+              sum128<S>(Rh[c0r + q], Rl[c0r + q], hi, lo);
+              xw[r] = cv[q] - scale_round(hi, lo, eW + eYs[r] - 14 - 7 * (S - 1) + 7 * S - 1);
+            }
           }
         }
       }
@@ -609,7 +610,8 @@ evd_status_t launch_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   evd_status_t st = ensure_dynamic_smem((const void*)k_bcback_wave<S>, smem);
   if (st != EVD_OK) return st;
   WaveArgs a;
-  a.X = Q; a.ldx = ldq; a.n = n; a.R0 = R0; a.gstride = 2 * b; a.h0 = hh0; a.h = 2 * b - 1;
+  a.X = reinterpret_cast<long long*>(Q); a.ldx = ldq; a.n = n; a.R0 = R0; a.gstride = 2 * b; a.h0 = hh0;
+  a.h = 2 * b - 1;
   a.Vb = Vb; a.eV = eV; a.Yb = Yb; a.eY = eY; a.st = pc.status;
   dim3 grid((unsigned)ceil_div(n, OZ_BM), (unsigned)count);
   // executed bf16 flops of the two products (tensor work of one wave)
@@ -622,7 +624,42 @@ evd_status_t launch_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   return EVD_OK;
 }
 
+// X (FP64, in place) <-> fixed point T = round_half_away(x 2^(7S - 1)) (int64).
+template <int S>
+__global__ void k_x_fixed(double* Q, int64_t ldq, int64_t n, int to_fixed) {
+  const int64_t j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double* p = Q + i + j * ldq;
+    if (to_fixed) {
+      const double x = *p;
+      const long long T = ozaki_scaled(x, 1, S);
+      *reinterpret_cast<long long*>(p) = T;
+    } else {
+      const long long T = *reinterpret_cast<const long long*>(p);
+      *p = (double)T * (1.0 / (double)(1ll << (7 * S - 1)));
+    }
+  }
+}
+
+template <int S>
+evd_status_t fixed_point(double* Q, int64_t ldq, int64_t n, bool to_fixed, cudaStream_t s) {
+  for (int64_t j0 = 0; j0 < n; j0 += 65535) {
+    const int64_t cols = std::min<int64_t>(n - j0, 65535);
+    k_x_fixed<S><<<dim3((unsigned)std::min<int64_t>(ceil_div(n, 256), 16), (unsigned)cols), 256, 0, s>>>(
+        Q + j0 * ldq, ldq, n, to_fixed ? 1 : 0);
+    count_launch();
+  }
+  EVD_CUDA_TRY(cudaGetLastError());
+  return EVD_OK;
+}
+
 }  // namespace
+
+evd_status_t bcback_fixed_point(const PlanCore& pc, double* Q, int64_t ldq, bool to_fixed) {
+  StatScope sc("bc_back_prep", pc.stream);
+  return (pc.slices == 8) ? fixed_point<8>(Q, ldq, pc.n, to_fixed, pc.stream)
+                          : fixed_point<6>(Q, ldq, pc.n, to_fixed, pc.stream);
+}
 
 bool bcback_fused_supported(const PlanCore& pc) {
   return pc.b == BB_G && (pc.slices == 8 || pc.slices == 6) && pc.n >= 1024;

@@ -251,7 +251,10 @@ def ours(args):
     with torch.no_grad():
         lam_t = torch.from_numpy(lam).cuda()
         dlam = float((w - lam_t).abs().max().item())
-        cols = torch.arange(n, device="cuda") if n <= 8192 else torch.randperm(n, device="cuda")[:256]
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(n)
+        cols = (torch.arange(n, device="cuda") if n <= 8192
+                else torch.randperm(n, device="cuda", generator=gen)[:256])
         Qs = Q[:, cols]
         A0s = A0
         R = A0s @ Qs - Qs * w[cols][None, :]

@@ -10,10 +10,12 @@
 //            The CTA's converter warps read the fixed-point tile of X, write its
 //            digits straight into shared memory; V's slices come pre-split.
 //   exact    D1 drained into exact 128-bit integer sums (W^T times a power of two).
-//   phase 2  D2[m][r] = sum_i W^T(m, i) Y(r, i)              M = 128, N = 128 (two
-//            halves of 64), K = g = 64.  W^T is split in the CTA straight from the
-//            integer sums (per-row scale, integer rescaling and rounding),
-//            Y's slices come pre-split; X(R0 + r, c0 + m) -= D2[m][r].
+//   phase 2  D2[r][c] = sum_i Y(r, i) W(i, c)                 M = 128 rows, N = 128
+//            columns (two halves of 64), K = g = 64.  W is split in the CTA straight
+//            from the integer sums (scale per column of X, integer rescaling and
+//            rounding), Y's slices come pre-split; X(R0 + r, c0 + c) -= D2[r][c].
+//            The accumulator's lanes are rows of X, so each warp of the epilogue
+//            reads and writes 32 consecutive elements of one column.
 // X is kept in fixed point during BC-Back: T = round(x 2^(7S - 1)) in int64, in
 // place of the FP64 values (bcback_fixed_point converts on entry and exit).  X is
 // orthogonal (D&C's eigenvectors times orthogonal reflectors), so |x| < 2 and
@@ -25,8 +27,8 @@
 //
 // Roles (576 threads): warp 0 copies the pre-split blobs (bulk copies), warp 1
 // owns the tensor memory (512 columns) and issues the MMAs, warps 2..17 convert X
-// and W into slices and drain the accumulators (16 columns per thread).  Every
-// wait is bounded.
+// and W into slices and drain the accumulators (16 accumulator columns per
+// thread).  Every wait is bounded.
 #include <algorithm>
 #include <cstdio>
 
@@ -60,7 +62,7 @@ __device__ __forceinline__ int frexp_exp(int biased_max) { return (biased_max > 
 //                 T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i)
 //   product       Y_p = V_p T_p                           (batched split product)
 //   k_bb_split    slices of V (B operand of phase 1: N = i, K = r, scale per i) and
-//                 of Y (B operand of phase 2: N = r, K = i, scale per r)
+//                 of Y (A operand of phase 2: M = r, K = i, scale per r)
 // Problem p of wave t is the group J' = jp0 + p, J = nJ - 1 - J', k = t - J'.
 __global__ void __launch_bounds__(256) k_bb_gather(const double* __restrict__ U, const double* __restrict__ Utau,
                                                    int64_t n, int b, int64_t nJ, int64_t t, int64_t jp0, double* Vg,
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(256) k_bb_split(const double* __restrict__ Vg,
         h2.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q + 1], S, tt));
         w[q] = *reinterpret_cast<uint32_t*>(&h2);
       }
-      *reinterpret_cast<uint4*>(Yp + blob_index(r, i0, tt, S, 64, g / 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(Yp + blob_index(r, i0, tt, S, 128, g / 16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -260,9 +262,17 @@ __device__ __forceinline__ long long scale_round(long long hi, unsigned long lon
   return (hi < 0) ? -(long long)m : (long long)m;
 }
 
+// The exact integer value of an FP32 accumulator v with |v| < 2^22: v + 1.5 * 2^23
+// lies in [2^23, 2^24), where the float's ulp is 1, so the integer is its low
+// mantissa bits (one add and one integer subtract instead of a conversion).
+__device__ __forceinline__ int f2i_exact22(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
+
 // Drain the S weight accumulators of this thread's 16 columns (TMEM lane quadrant
-// `quad`, columns 16 q4 .. +15 of each weight) into the two exact sums.
-template <int S>
+// `quad`, columns 16 q4 .. +15 of each weight) into the two exact sums.  KMAX is
+// the product's K.  Top digits are at most 128 in magnitude, the others 64, so
+// accumulator k (the pairs t + u = k) is bounded by KMAX 128^2 for k = 0 and by
+// KMAX (2 128 64 + (k - 1) 64^2) for k >= 1; below 2^22 the add trick converts it.
+template <int S, int KMAX>
 __device__ __forceinline__ void drain16(uint32_t tmem, int quad, int q4, long long* Rh, long long* Rl) {
   constexpr int L = S - 1, H = (L < 3) ? L : 3;
 #pragma unroll
@@ -271,34 +281,57 @@ __device__ __forceinline__ void drain16(uint32_t tmem, int quad, int q4, long lo
   for (int k = 0; k <= L; ++k) {
     float v[16];
     tc_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + q4 * 16), v);
+    const long long bound = (long long)KMAX * ((k == 0) ? 128 * 128 : 2 * 128 * 64 + (k - 1) * 64 * 64);
+    const bool small = bound < (1ll << 22);
+    int iv[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) iv[c] = small ? f2i_exact22(v[c]) : __float2int_rn(v[c]);
     if (k <= 3) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) Rh[c] += (long long)__float2int_rn(v[c]) << (7 * (H - k));
+      for (int c = 0; c < 16; ++c) Rh[c] += (long long)iv[c] << (7 * (H - k));
     } else {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) Rl[c] += (long long)__float2int_rn(v[c]) << (7 * (L - k));
+      for (int c = 0; c < 16; ++c) Rl[c] += (long long)iv[c] << (7 * (L - k));
     }
   }
 }
 
-// Write the S digit slices of n consecutive K-values (already scaled integers T,
-// n = 4 or 8, kk0 a multiple of n) into a K-major blob with 128-row tiles: row m,
-// K-elements kk0 .. kk0+n-1 of the blob's K-step.
-template <int S, int NV>
+// Digit t >= 1 of two offset integers as a bf16 pair: the 7-bit field f in
+// [0, 127] placed under the exponent of 128 (bits 0x4300 | f, the value 128 + f
+// exactly), minus 192 gives the digit f - 64 exactly.
+__device__ __forceinline__ uint32_t digit_pair(long long TOa, long long TOb, int sh) {
+  const uint32_t fa = (uint32_t)(TOa >> sh) & 127u, fb = (uint32_t)(TOb >> sh) & 127u;
+  const uint32_t w = 0x43004300u | fa | (fb << 16), c192 = 0x43404340u;
+  const __nv_bfloat162 v =
+      __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&w), *reinterpret_cast<const __nv_bfloat162*>(&c192));
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Write the S digit slices of NV consecutive K-values (already scaled integers T,
+// NV = 4 or 8, kk0 a multiple of NV) into a K-major blob of TR-row tiles: row m,
+// K-elements kk0 .. kk0+NV-1 of the blob's K-step.
+template <int S, int NV, int TR>
 __device__ __forceinline__ void put_digits(uint8_t* blob_ks, int m, int kk0, const long long* T) {
   const long long off = ozaki_offset(S);
   const int core = ((m >> 3) * 2 + (kk0 >> 3)) * 64 + (m & 7) * 8 + (kk0 & 7);  // elements
+  long long TO[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) TO[q] = T[q] + off;
 #pragma unroll
   for (int tt = 0; tt < S; ++tt) {
     uint32_t w[NV / 2];
 #pragma unroll
     for (int q = 0; q < NV / 2; ++q) {
-      __nv_bfloat162 h2;
-      h2.x = __float2bfloat16_rn((float)ozaki_digit(T[2 * q] + off, S, tt));
-      h2.y = __float2bfloat16_rn((float)ozaki_digit(T[2 * q + 1] + off, S, tt));
-      w[q] = *reinterpret_cast<uint32_t*>(&h2);
+      if (tt == 0) {  // the signed top digit (|d| <= 128, exact in bf16), made a float by the add trick
+        const float da = __int_as_float(0x4B400000 + (int)(TO[2 * q] >> (7 * (S - 1)))) - 12582912.0f;
+        const float db = __int_as_float(0x4B400000 + (int)(TO[2 * q + 1] >> (7 * (S - 1)))) - 12582912.0f;
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(da, db);
+        w[q] = *reinterpret_cast<const uint32_t*>(&h2);
+      } else {
+        w[q] = digit_pair(TO[2 * q], TO[2 * q + 1], 7 * (S - 1 - tt));
+      }
     }
-    uint8_t* dst = blob_ks + ((size_t)tt * OZ_BM * OZ_KS + core) * 2;
+    uint8_t* dst = blob_ks + ((size_t)tt * TR * OZ_KS + core) * 2;
     if (NV == 8) *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2 % (NV / 2)], w[3 % (NV / 2)]);
     else *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
   }
@@ -310,18 +343,20 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2;   // one K-step of a 128-row operand (all slices)
   constexpr uint32_t B_KS = S * OZ_BN * OZ_KS * 2;   // one K-step of a 64-row operand
-  // phase 1: A stages [0, 3 A_KS), B stages after; phase 2: W blob [0, 4 A_KS), Y half after
+  // phase 1: A stages [0, 3 A_KS), B stages after; phase 2: Y (all K-steps) at 0,
+  // one half of W (64 columns, all K-steps) after it
   constexpr uint32_t P1_B = BB_P1_STAGES * A_KS;
-  constexpr uint32_t P2_Y = 4 * A_KS;
-  constexpr uint32_t DATA = (P1_B + BB_P1_STAGES * B_KS > P2_Y + 4 * B_KS) ? P1_B + BB_P1_STAGES * B_KS
-                                                                            : P2_Y + 4 * B_KS;
+  constexpr uint32_t P2_Y = 0;
+  constexpr uint32_t P2_W = 4 * A_KS;
+  constexpr uint32_t DATA = (P1_B + BB_P1_STAGES * B_KS > P2_W + 4 * B_KS) ? P1_B + BB_P1_STAGES * B_KS
+                                                                            : P2_W + 4 * B_KS;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + DATA);
   uint64_t* fullA = bars;                          // [3], 16 arrivals (converter warps)
   uint64_t* fullB = bars + 3;                      // [3], 1 arrival + bytes
   uint64_t* empty = bars + 6;                      // [3], MMA commit
   uint64_t* acc1 = bars + 9;                       // phase 1 accumulators ready
-  uint64_t* fullW = bars + 10;                     // W slices written (16 arrivals)
-  uint64_t* fullY = bars + 11;                     // Y half copied (1 arrival + bytes), two phases
+  uint64_t* fullW = bars + 10;                     // W half written (8 arrivals), two phases
+  uint64_t* fullY = bars + 11;                     // Y copied (1 arrival + bytes)
   uint64_t* acc2 = bars + 12;                      // phase 2 half ready (two phases)
   uint64_t* drained = bars + 13;                   // epilogue drained phase 2 half 0 (16 arrivals)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
@@ -329,6 +364,7 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
   int* eVs = reinterpret_cast<int*>(tmem_slot + 4);        // 64
   int* eYs = eVs + BB_G;                                     // 128
   int* exw = eYs + BB_H;                                     // 4 x 128 (per-quarter maxima)
+  int* eWs = exw + 4 * BB_H;                                 // 128, scale of W per column of X
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = blockIdx.y;
   const int64_t c0 = (int64_t)blockIdx.x * OZ_BM;
@@ -344,7 +380,7 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
       mbar_init(smem_u32(empty + i), 1);
     }
     mbar_init(smem_u32(acc1), 1);
-    mbar_init(smem_u32(fullW), 16);
+    mbar_init(smem_u32(fullW), 8);
     mbar_init(smem_u32(fullY), 1);
     mbar_init(smem_u32(acc2), 1);
     mbar_init(smem_u32(drained), 16);
@@ -380,14 +416,9 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
       }
       // phase 1 finished reading shared memory before the Y copy may overwrite it
       if (!*abort && mbar_wait(smem_u32(acc1), 0, abort, a.st, 9102)) {
-        mbar_expect_tx(smem_u32(fullY), 4 * B_KS);
-        bulk_load(smem_u32(smem + P2_Y), Yp, 4 * B_KS, smem_u32(fullY));
-        // half 1 after the half-0 products have read the buffer
-        if (mbar_wait(smem_u32(acc2), 0, abort, a.st, 9103)) {
-          mbar_expect_tx(smem_u32(fullY), 4 * B_KS);
-          bulk_load(smem_u32(smem + P2_Y), Yp + (size_t)4 * S * OZ_BN * OZ_KS, 4 * B_KS, smem_u32(fullY));
-          mbar_wait(smem_u32(fullY), 1, abort, a.st, 9104);  // let the copy land before leaving
-        }
+        mbar_expect_tx(smem_u32(fullY), 4 * A_KS);
+        bulk_load(smem_u32(smem + P2_Y), Yp, 4 * A_KS, smem_u32(fullY));
+        mbar_wait(smem_u32(fullY), 0, abort, a.st, 9104);  // let the copy land before leaving
       }
     }
   } else if (warp == 1) {
@@ -408,14 +439,14 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
       if (ok) tc_commit(smem_u32(acc1));
       // phase 2, half 0 then half 1 (the epilogue drains half 0 in between)
       for (int hf = 0; hf < 2 && ok; ++hf) {
-        ok = mbar_wait(smem_u32(fullY), hf, abort, a.st, 9113);
-        if (ok && hf == 0) ok = mbar_wait(smem_u32(fullW), 0, abort, a.st, 9114);
+        if (hf == 0) ok = mbar_wait(smem_u32(fullY), 0, abort, a.st, 9113);
+        if (ok) ok = mbar_wait(smem_u32(fullW), hf, abort, a.st, 9114);
         if (ok && hf == 1) ok = mbar_wait(smem_u32(drained), 0, abort, a.st, 9115);
         if (!ok) break;
         tc_fence_after();
         for (int ks = 0; ks < BB_G / OZ_KS; ++ks)
-          issue_stage<S>(tmem, dbase + (uint64_t)((ks * A_KS) >> 4), dbase + (uint64_t)((P2_Y + ks * B_KS) >> 4),
-                         ks > 0 ? 1u : 0u);
+          issue_stage<S>(tmem, dbase + (uint64_t)((P2_Y + ks * A_KS) >> 4),
+                         dbase + (uint64_t)((P2_W + ks * B_KS) >> 4), ks > 0 ? 1u : 0u);
         tc_commit(smem_u32(acc2));
       }
     }
@@ -435,26 +466,30 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
     // |x| < 2 and |T| < 2^(7S)).
     constexpr int eA = 1;
     bool ok = true;
-    long long xn[4];
+    long long xn[4], xnn[4];  // the next two K-steps' values, loaded ahead
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = kq * 4 + q;
       xn[q] = (colok && r < hp) ? xc[r] : 0ll;
+      xnn[q] = (colok && r + OZ_KS < hp) ? xc[r + OZ_KS] : 0ll;
     }
     for (int j = 0; j < BB_H / OZ_KS; ++j) {
       const int si = j % 3, round = j / 3;
       long long T[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) T[q] = xn[q];
-      if (j + 1 < BB_H / OZ_KS) {  // the next K-step's values, loaded ahead
+      for (int q = 0; q < 4; ++q) {
+        T[q] = xn[q];
+        xn[q] = xnn[q];
+      }
+      if (j + 2 < BB_H / OZ_KS) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int r = (j + 1) * OZ_KS + kq * 4 + q;
-          xn[q] = (colok && r < hp) ? xc[r] : 0ll;
+          const int r = (j + 2) * OZ_KS + kq * 4 + q;
+          xnn[q] = (colok && r < hp) ? xc[r] : 0ll;
         }
       }
       if (ok && round > 0) ok = mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9121);
-      if (ok) put_digits<S, 4>(smem + si * A_KS, m, kq * 4, T);
+      if (ok) put_digits<S, 4, OZ_BM>(smem + si * A_KS, m, kq * 4, T);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       ok = __all_sync(0xffffffffu, ok);
       if (ok && lane == 0) mbar_arrive(smem_u32(fullA + si));
@@ -470,7 +505,7 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
       int bmax = -100000;  // max over this thread's columns of bitlen(R) + scale
       if (ok) {
         tc_fence_after();
-        drain16<S>(tmem, quad, q4, Rh, Rl);
+        drain16<S, BB_H>(tmem, quad, q4, Rh, Rl);
         tc_fence_before();
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
@@ -487,56 +522,73 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
       const int e4 = max(max(exw[m2], exw[BB_H + m2]), max(exw[2 * BB_H + m2], exw[3 * BB_H + m2]));
       eW = (e4 > -100000) ? e4 : -1022;
     }
+    if (q4 == 0) eWs[m2] = eW;
+    // W(i, m2), i = 16 q4 .. +15, scaled to the integer grid of its column
+    // (integer rescaling of the exact sums, no FP64 round trip): K-step q4 of the
+    // B operand of phase 2, half m2 / 64 of the columns
+    long long T[16];
     if (ok) {
-      // W^T slices, K = i: this thread's 16 columns are K-step q4 (integer rescaling
-      // of the exact sums, no FP64 round trip)
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        long long T[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = 8 * u + q;
-          long long hi;
-          unsigned long long lo;
-          sum128<S>(Rh[c], Rl[c], hi, lo);
-          T[q] = scale_round(hi, lo, eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1) + 7 * S - eW);
-        }
-        put_digits<S, 8>(smem + q4 * A_KS, m2, 8 * u, T);
+      for (int c = 0; c < 16; ++c) {
+        long long hi;
+        unsigned long long lo;
+        sum128<S>(Rh[c], Rl[c], hi, lo);
+        T[c] = scale_round(hi, lo, eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1) + 7 * S - eW);
       }
+    }
+    const bool upper = quad >= 2;  // columns 64 .. 127: written once half 0's products are done
+    if (ok && !upper) {
+      put_digits<S, 8, OZ_BN>(smem + P2_W + q4 * B_KS, m2, 0, T);
+      put_digits<S, 8, OZ_BN>(smem + P2_W + q4 * B_KS, m2, 8, T + 8);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(fullW));
     }
-    // phase 2: X(R0 + r, c0 + m2) -= D2[m2][r], r = 64 hf + 16 q4 + c
-    const int64_t colw = c0 + m2;
-    long long* xw = a.X + colw * a.ldx + R0;
-    for (int hf = 0; hf < 2 && ok; ++hf) {
-      const int rb = 64 * hf + 16 * q4;
-      ok = mbar_wait(smem_u32(acc2), hf, abort, a.st, 9123);
+    ok = bar_and_epi(ok);  // eWs complete
+    // phase 2: X(R0 + r, c0 + 64 hf + 16 q4 + c) -= D2[r][64 hf + 16 q4 + c], r = m2
+    const int r = m2;
+    const bool rok = r < hp;
+    const int eYr = eYs[r];
+    long long* xr = a.X + R0 + r;
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      if (ok) ok = mbar_wait(smem_u32(acc2), hf, abort, a.st, 9123);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
+      if (hf == 0 && upper) {
+        // half 0's products have read the W buffer: the upper half goes in
+        put_digits<S, 8, OZ_BN>(smem + P2_W + q4 * B_KS, m2 - 64, 0, T);
+        put_digits<S, 8, OZ_BN>(smem + P2_W + q4 * B_KS, m2 - 64, 8, T + 8);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(fullW));
+      }
       tc_fence_after();
-      drain16<S>(tmem, quad, q4, Rh, Rl);
+      drain16<S, BB_G>(tmem, quad, q4, Rh, Rl);
       tc_fence_before();
       __syncwarp();
       if (hf == 0 && lane == 0) mbar_arrive(smem_u32(drained));
-      if (colw < a.n) {
+      // delta = R 2^(eW_c + eY_r - 14 - 7L) on the grid 2^(1 - 7S), rounded once
+      const int cb = 64 * hf + 16 * q4;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        long long hi;
+        unsigned long long lo;
+        sum128<S>(Rh[c], Rl[c], hi, lo);
+        Rh[c] = scale_round(hi, lo, eWs[cb + c] + eYr - 14 - 7 * (S - 1) + 7 * S - 1);
+      }
+      long long* xc2 = xr + (c0 + cb) * a.ldx;
+      const int64_t left = a.n - (c0 + cb);
+      const int ncol = left < 16 ? (int)left : 16;
+      if (rok) {
 #pragma unroll
         for (int c0r = 0; c0r < 16; c0r += 8) {
           long long cv[8];  // the 8 loads go out before any store
 #pragma unroll
-          for (int q = 0; q < 8; ++q) cv[q] = (rb + c0r + q < hp) ? xw[rb + c0r + q] : 0ll;
+          for (int q = 0; q < 8; ++q) cv[q] = (c0r + q < ncol) ? xc2[(c0r + q) * a.ldx] : 0ll;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int r = rb + c0r + q;
-            if (r < hp) {
-              // delta = R 2^(eW + eY_r - 14 - 7L) on the grid 2^(1 - 7S), rounded once
-              long long hi;
-              unsigned long long lo;
-              sum128<S>(Rh[c0r + q], Rl[c0r + q], hi, lo);
-              xw[r] = cv[q] - scale_round(hi, lo, eW + eYs[r] - 14 - 7 * (S - 1) + 7 * S - 1);
-            }
-          }
+          for (int q = 0; q < 8; ++q)
+            if (c0r + q < ncol) xc2[(c0r + q) * a.ldx] = cv[q] - Rh[c0r + q];
         }
       }
     }
@@ -553,7 +605,7 @@ template <int S>
 size_t wave_smem_bytes() {
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2, B_KS = S * OZ_BN * OZ_KS * 2;
   constexpr uint32_t P1 = BB_P1_STAGES * A_KS + BB_P1_STAGES * B_KS, P2 = 4 * A_KS + 4 * B_KS;
-  return 1024 + (P1 > P2 ? P1 : P2) + 14 * 8 + 16 + (BB_G + BB_H + 4 * BB_H) * 4 + 64;
+  return 1024 + (P1 > P2 ? P1 : P2) + 14 * 8 + 16 + (BB_G + BB_H + 5 * BB_H) * 4 + 64;
 }
 
 template <int S>

@@ -29,8 +29,11 @@
 // owns the tensor memory (512 columns) and issues the MMAs, warps 2..17 convert X
 // and W into slices and drain the accumulators (16 accumulator columns per
 // thread).  Every wait is bounded.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "device_util.cuh"
 #include "evd_internal.h"
@@ -47,6 +50,8 @@ constexpr int BB_G = 64;          // group size g = b
 constexpr int BB_H = 128;         // padded rows of a group (h = 2b - 1 = 127)
 constexpr int BB_THREADS = 576;  // warp 0 copies, warp 1 MMA, warps 2..17 convert and drain
 constexpr int BB_P1_STAGES = 3;
+constexpr int BB_XROWS = OZ_KS + 2;                       // rows of an X box (starts on an even row)
+constexpr uint32_t BB_XS = BB_XROWS * OZ_BM * 8;          // one X K-step in shared memory (int64)
 
 __device__ __forceinline__ int biased_exp(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
@@ -186,6 +191,7 @@ __global__ void __launch_bounds__(256) k_bb_split(const double* __restrict__ Vg,
 
 // ---------------------------------------------------------------- fused wave
 struct WaveArgs {
+  CUtensorMap xmap;  // X as a 2-D int64 tensor (rows, columns), box BB_XROWS x 128
   long long* X;     // X in fixed point: x = T 2^(1 - 7S) (see bcback_fixed_point)
   int64_t ldx, n;
   int64_t R0;       // first row of group 0
@@ -224,41 +230,42 @@ __device__ __forceinline__ void sum128(long long rh, long long rl, long long& hi
   }
 }
 
+// 64-bit shifts with PTX semantics: an amount above 64 (a negative int passed as
+// unsigned included) is clamped to 64, which gives 0.
+__device__ __forceinline__ unsigned long long shl64(unsigned long long x, uint32_t k) {
+  unsigned long long r;
+  asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(k));
+  return r;
+}
+__device__ __forceinline__ unsigned long long shr64(unsigned long long x, uint32_t k) {
+  unsigned long long r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(k));
+  return r;
+}
+
 // Magnitude (uh, ul) of a signed 128-bit value, and its bit length (0 for zero).
+// Branch-free, so that the 16 values of a thread interleave.
 __device__ __forceinline__ int abs128(long long hi, unsigned long long lo, unsigned long long& uh,
                                       unsigned long long& ul) {
-  uh = (unsigned long long)hi;
-  ul = lo;
-  if (hi < 0) {
-    ul = ~ul + 1ull;
-    uh = ~uh + (ul == 0ull ? 1ull : 0ull);
-  }
-  if (uh) return 128 - __clzll((long long)uh);
-  if (ul) return 64 - __clzll((long long)ul);
-  return 0;
+  const unsigned long long sg = (unsigned long long)(hi >> 63);  // all ones when negative
+  ul = (lo ^ sg) - sg;
+  uh = ((unsigned long long)hi ^ sg) + ((sg != 0ull && ul == 0ull) ? 1ull : 0ull);
+  const int bh = 64 - __clzll((long long)uh), bl = 64 - __clzll((long long)ul);
+  return uh ? 64 + bh : bl;
 }
 
 // T = round_half_away(R 2^d) for a signed 128-bit R with |R 2^d| < 2^62.
+// d >= 0: |R| < 2^(62 - d) sits in the low word.  d = -k < 0: add 2^(k-1) to the
+// magnitude and shift it right by k (k >= 128 gives 0).  Branch-free: the shift
+// amounts out of range clamp to a zero contribution.
 __device__ __forceinline__ long long scale_round(long long hi, unsigned long long lo, int d) {
   unsigned long long uh, ul;
   abs128(hi, lo, uh, ul);
-  unsigned long long m;
-  if (d >= 0) {
-    m = (d < 64) ? (ul << d) : 0ull;  // |R| < 2^(62 - d): the magnitude sits in the low word (R = 0 for d >= 62)
-  } else {
-    const int k = -d;
-    if (k >= 128) return 0;
-    // add half an ulp of the result, then shift right by k
-    if (k - 1 < 64) {
-      const unsigned long long add = 1ull << (k - 1);
-      const unsigned long long nl = ul + add;
-      uh += (nl < ul) ? 1ull : 0ull;
-      ul = nl;
-    } else {
-      uh += 1ull << (k - 1 - 64);
-    }
-    m = (k < 64) ? ((ul >> k) | (uh << (64 - k))) : (uh >> (k - 64));
-  }
+  const uint32_t k = (uint32_t)(-d);
+  const unsigned long long nl = ul + shl64(1ull, k - 1u);
+  const unsigned long long nh = uh + shl64(1ull, k - 65u) + (nl < ul ? 1ull : 0ull);
+  const unsigned long long mr = shr64(nl, k) | shl64(nh, 64u - k) | shr64(nh, k - 64u);
+  const unsigned long long m = (d >= 0) ? shl64(ul, (uint32_t)d) : mr;
   return (hi < 0) ? -(long long)m : (long long)m;
 }
 
@@ -338,18 +345,19 @@ __device__ __forceinline__ void put_digits(uint8_t* blob_ks, int m, int kk0, con
 }
 
 template <int S>
-__global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a) {
+__global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_constant__ WaveArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2;   // one K-step of a 128-row operand (all slices)
   constexpr uint32_t B_KS = S * OZ_BN * OZ_KS * 2;   // one K-step of a 64-row operand
-  // phase 1: A stages [0, 3 A_KS), B stages after; phase 2: Y (all K-steps) at 0,
-  // one half of W (64 columns, all K-steps) after it
+  // phase 1: A stages [0, 3 A_KS), B stages, then the X boxes; phase 2: Y (all
+  // K-steps) at 0, one half of W (64 columns, all K-steps) after it
   constexpr uint32_t P1_B = BB_P1_STAGES * A_KS;
+  constexpr uint32_t P1_X = P1_B + BB_P1_STAGES * B_KS;
   constexpr uint32_t P2_Y = 0;
   constexpr uint32_t P2_W = 4 * A_KS;
-  constexpr uint32_t DATA = (P1_B + BB_P1_STAGES * B_KS > P2_W + 4 * B_KS) ? P1_B + BB_P1_STAGES * B_KS
-                                                                            : P2_W + 4 * B_KS;
+  constexpr uint32_t DATA = (P1_X + BB_P1_STAGES * BB_XS > P2_W + 4 * B_KS) ? P1_X + BB_P1_STAGES * BB_XS
+                                                                             : P2_W + 4 * B_KS;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + DATA);
   uint64_t* fullA = bars;                          // [3], 16 arrivals (converter warps)
   uint64_t* fullB = bars + 3;                      // [3], 1 arrival + bytes
@@ -359,7 +367,8 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
   uint64_t* fullY = bars + 11;                     // Y copied (1 arrival + bytes)
   uint64_t* acc2 = bars + 12;                      // phase 2 half ready (two phases)
   uint64_t* drained = bars + 13;                   // epilogue drained phase 2 half 0 (16 arrivals)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
+  uint64_t* fullX = bars + 14;                     // [3], X box landed (1 arrival + bytes)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 17);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* eVs = reinterpret_cast<int*>(tmem_slot + 4);        // 64
   int* eYs = eVs + BB_G;                                     // 128
@@ -378,6 +387,7 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
       mbar_init(smem_u32(fullA + i), 16);
       mbar_init(smem_u32(fullB + i), 1);
       mbar_init(smem_u32(empty + i), 1);
+      mbar_init(smem_u32(fullX + i), 1);
     }
     mbar_init(smem_u32(acc1), 1);
     mbar_init(smem_u32(fullW), 8);
@@ -400,19 +410,35 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- copies: V K-steps (phase 1), then the two Y halves
+      // ---------------- copies: per K-step of phase 1 the X box (tensor copy: rows
+      // x0 .. x0 + 17 from the even row x0 = R0 + 16 j - (R0 & 1), columns c0 ..
+      // c0 + 127, zero outside X) and V's slices; then Y
+      const uint64_t xmap = reinterpret_cast<uint64_t>(&a.xmap);
       int issued = 0;
       for (int j = 0; j < BB_H / OZ_KS; ++j) {
         const int si = j % 3, round = j / 3;
-        if (round > 0 && !mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9101)) break;
+        // the converters are done with box si once they have filled A stage si
+        if (round > 0 && !mbar_wait(smem_u32(fullA + si), (round - 1) & 1, abort, a.st, 9100)) break;
+        mbar_expect_tx(smem_u32(fullX + si), BB_XS);
+        const int x0 = (int)(R0 + (int64_t)j * OZ_KS - (R0 & 1)), y0 = (int)c0;
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(smem_u32(smem + P1_X + si * BB_XS)), "l"(xmap), "r"(x0), "r"(y0), "r"(smem_u32(fullX + si))
+            : "memory");
+        if (round > 0 && !mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9101)) {
+          ++issued;
+          break;
+        }
         mbar_expect_tx(smem_u32(fullB + si), B_KS);
         bulk_load(smem_u32(smem + P1_B + si * B_KS), Vp + (size_t)j * S * OZ_BN * OZ_KS, B_KS, smem_u32(fullB + si));
         ++issued;
       }
       if (*abort) {
         // let the copies already in flight land before the CTA exits
-        for (int j = (issued > 3 ? issued - 3 : 0); j < issued; ++j)
+        for (int j = (issued > 3 ? issued - 3 : 0); j < issued; ++j) {
+          for (long long i = 0; i < OZ_WAIT_LIMIT && !mbar_try(smem_u32(fullX + j % 3), (j / 3) & 1); ++i) {}
           for (long long i = 0; i < OZ_WAIT_LIMIT && !mbar_try(smem_u32(fullB + j % 3), (j / 3) & 1); ++i) {}
+        }
       }
       // phase 1 finished reading shared memory before the Y copy may overwrite it
       if (!*abort && mbar_wait(smem_u32(acc1), 0, abort, a.st, 9102)) {
@@ -458,36 +484,19 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const WaveArgs a)
     const int ct = threadIdx.x - 64;
     // phase 1 producer mapping: column m = ct / 4, rows 4 kq .. 4 kq + 3 of a K-step
     const int m = ct >> 2, kq = ct & 3;
-    const int64_t col = c0 + m;
-    const bool colok = col < a.n;
-    const long long* xc = a.X + col * a.ldx + R0;
     // X is held in fixed point on the grid 2^(1 - 7S): the split of the X operand
     // with the fixed scale 2^1 is then the integer itself (X is orthogonal, so
     // |x| < 2 and |T| < 2^(7S)).
     constexpr int eA = 1;
+    const int xoff = (int)(R0 & 1);  // row R0 + 16 j sits at row xoff of its box
     bool ok = true;
-    long long xn[4], xnn[4];  // the next two K-steps' values, loaded ahead
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = kq * 4 + q;
-      xn[q] = (colok && r < hp) ? xc[r] : 0ll;
-      xnn[q] = (colok && r + OZ_KS < hp) ? xc[r + OZ_KS] : 0ll;
-    }
     for (int j = 0; j < BB_H / OZ_KS; ++j) {
       const int si = j % 3, round = j / 3;
       long long T[4];
+      if (ok) ok = mbar_wait(smem_u32(fullX + si), round & 1, abort, a.st, 9120);
+      const long long* xs = reinterpret_cast<const long long*>(smem + P1_X + si * BB_XS) + m * BB_XROWS + kq * 4 + xoff;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        T[q] = xn[q];
-        xn[q] = xnn[q];
-      }
-      if (j + 2 < BB_H / OZ_KS) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int r = (j + 2) * OZ_KS + kq * 4 + q;
-          xnn[q] = (colok && r < hp) ? xc[r] : 0ll;
-        }
-      }
+      for (int q = 0; q < 4; ++q) T[q] = (ok && j * OZ_KS + kq * 4 + q < hp) ? xs[q] : 0ll;
       if (ok && round > 0) ok = mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9121);
       if (ok) put_digits<S, 4, OZ_BM>(smem + si * A_KS, m, kq * 4, T);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -605,7 +614,26 @@ template <int S>
 size_t wave_smem_bytes() {
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2, B_KS = S * OZ_BN * OZ_KS * 2;
   constexpr uint32_t P1 = BB_P1_STAGES * A_KS + BB_P1_STAGES * B_KS, P2 = 4 * A_KS + 4 * B_KS;
-  return 1024 + (P1 > P2 ? P1 : P2) + 14 * 8 + 16 + (BB_G + BB_H + 5 * BB_H) * 4 + 64;
+  constexpr uint32_t P1X = P1 + BB_P1_STAGES * BB_XS;
+  return 1024 + (P1X > P2 ? P1X : P2) + 17 * 8 + 16 + (BB_G + BB_H + 5 * BB_H) * 4 + 64;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the
+// driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
 }
 
 template <int S>
@@ -662,6 +690,19 @@ evd_status_t launch_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   evd_status_t st = ensure_dynamic_smem((const void*)k_bcback_wave<S>, smem);
   if (st != EVD_OK) return st;
   WaveArgs a;
+  {
+    // X (n x n int64, column stride ldq) for the tensor copies of phase 1
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return EVD_ERR_CUDA;
+    const cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)ldq * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)BB_XROWS, (cuuint32_t)OZ_BM};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&a.xmap, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, Q, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return EVD_ERR_CUDA;
+  }
   a.X = reinterpret_cast<long long*>(Q); a.ldx = ldq; a.n = n; a.R0 = R0; a.gstride = 2 * b; a.h0 = hh0;
   a.h = 2 * b - 1;
   a.Vb = Vb; a.eV = eV; a.Yb = Yb; a.eY = eY; a.st = pc.status;
@@ -713,8 +754,10 @@ evd_status_t bcback_fixed_point(const PlanCore& pc, double* Q, int64_t ldq, bool
                           : fixed_point<6>(Q, ldq, pc.n, to_fixed, pc.stream);
 }
 
-bool bcback_fused_supported(const PlanCore& pc) {
-  return pc.b == BB_G && (pc.slices == 8 || pc.slices == 6) && pc.n >= 1024;
+bool bcback_fused_supported(const PlanCore& pc, const double* Q, int64_t ldq) {
+  // the tensor copies of X want a 16-byte aligned base and column stride
+  return pc.b == BB_G && (pc.slices == 8 || pc.slices == 6) && pc.n >= 1024 && pc.n < ((int64_t)1 << 31) &&
+         ldq % 2 == 0 && (reinterpret_cast<uintptr_t>(Q) & 15) == 0;
 }
 
 evd_status_t bcback_fused_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,

@@ -169,7 +169,7 @@ struct BackWork {
 evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq,
                          const BackWork& w);
 // Fused BC-Back wave (b = 64, 6 or 8 slices; evd_bcback.cu).
-bool bcback_fused_supported(const PlanCore& pc);
+bool bcback_fused_supported(const PlanCore& pc, const double* Q, int64_t ldq);
 // X (FP64, in place) to and from the fixed point the fused waves work in.
 evd_status_t bcback_fixed_point(const PlanCore& pc, double* Q, int64_t ldq, bool to_fixed);
 evd_status_t bcback_fused_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,

@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "device_util.cuh"
 #include "evd_ozaki.h"
@@ -69,6 +70,7 @@ struct View {
   int64_t rows, K;
   int64_t pstride = 0;  // batched: element offset between consecutive problems
   int64_t K0 = -1;      // batched: K of problem 0 when >= 0 (a truncated first problem)
+  int64_t koff = 0;     // K-elements 0 .. koff-1 are zero, K-element kappa >= koff is p's kappa - koff
   __device__ __forceinline__ double get(int64_t r, int64_t k) const {
     if (mode == 0) return p[r + k * ld];
     if (mode == 1) return p[k + r * ld];
@@ -83,7 +85,7 @@ __device__ __forceinline__ void load_tile32(const View& v, int64_t r0, int64_t k
     const int a = idx & 31, b = idx >> 5;
     const int r = v.row_contig() ? a : b, k = v.row_contig() ? b : a;
     const int64_t R = r0 + r, KK = k0 + k;
-    t[r][k] = (R < v.rows && KK < v.K) ? v.get(R, KK) : 0.0;
+    t[r][k] = (R < v.rows && KK < v.K && KK >= v.koff) ? v.get(R, KK - v.koff) : 0.0;
   }
 }
 
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(256) k_split_fused(const View va, int* ea, __n
     for (int idx = tid; idx < total; idx += 256) {
       const int r = idx & 31, k = idx >> 5;
       const int64_t R = r0 + r;
-      tile[r * ls + k] = (R < v.rows && k < v.K) ? v.get(R, k) : 0.0;
+      tile[r * ls + k] = (R < v.rows && k < v.K && k >= v.koff) ? v.get(R, k - v.koff) : 0.0;
     }
   } else {
 #pragma unroll 8
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(256) k_split_fused(const View va, int* ea, __n
       const int t2 = idx >> 5;
       const int r = t2 & 31, k = ((t2 >> 5) << 5) + (idx & 31);
       const int64_t R = r0 + r;
-      tile[r * ls + k] = (R < v.rows && k < v.K) ? v.get(R, k) : 0.0;
+      tile[r * ls + k] = (R < v.rows && k < v.K && k >= v.koff) ? v.get(R, k - v.koff) : 0.0;
     }
   }
   __syncthreads();
@@ -234,6 +236,8 @@ struct MmaArgs {
   // p bn_pad + ... of B and writes C + p sC; problem 0 writes only m_first rows
   int batched;
   int64_t bm_pad, bn_pad, sC, m_first;
+  int64_t nkb_b;   // K-blocks per row tile of B's blob (A's is nkb)
+  int64_t c_skip;  // the first c_skip rows of the product are not stored; row r goes to row r - c_skip of C
 };
 
 __device__ __forceinline__ bool drain_after(int j, int nst) {
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int nst = (a.nst - j0 < a.stages_per_split) ? a.nst - j0 : a.stages_per_split;
   // blobs of this CTA's row tiles: stage j reads K-block j0 + j
   const __nv_bfloat16* blobA = a.SA + (size_t)((pb * a.bm_pad + m0) / OZ_BM) * a.nkb * s * (OZ_BM * OZ_KS);
-  const __nv_bfloat16* blobB = a.SB + (size_t)((pb * a.bn_pad + n0) / OZ_BN) * a.nkb * s * (OZ_BN * OZ_KS);
+  const __nv_bfloat16* blobB = a.SB + (size_t)((pb * a.bn_pad + n0) / OZ_BN) * a.nkb_b * s * (OZ_BN * OZ_KS);
   const int* ea = a.ea + pb * a.bm_pad;
   const int* eb = a.eb + pb * a.bn_pad;
   double* Cp = a.C + pb * a.sC;
@@ -396,11 +400,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         park[(2 * c) * 256] = Rh[c];
         park[(2 * c + 1) * 256] = Rl[c];
       }
-      if (row < m_lim) {
+      if (row >= a.c_skip && row < m_lim) {
         const int shift_hi = 7 * (L - H);  // R = R_hi 2^(7 (L - H)) + R_lo, value R 2^(e_r + f_c - 14 - 7L)
         const bool alpha_one = (a.alpha == 1.0), alpha_mone = (a.alpha == -1.0);
         const bool read_c = (a.part == nullptr) && (a.beta != 0.0);
-        double* crow = Cp + row;
+        double* crow = Cp + (row - a.c_skip);
+        const int64_t mo = a.m - a.c_skip;  // stored rows
 #pragma unroll 1
         for (int c0 = 0; c0 < 32; c0 += 4) {
           // the 4 loads of C go out before any store so that they overlap
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               }
               double v = i128_to_double(hi, lo, er + eb_s[half * 32 + cc] - 14 - 7 * L);
               if (a.part) {
-                a.part[(size_t)blockIdx.z * a.m * a.n + row + col * a.m] = v;
+                a.part[(size_t)blockIdx.z * mo * a.n + (row - a.c_skip) + col * mo] = v;
               } else {
                 if (alpha_mone) v = -v;
                 else if (!alpha_one) v *= a.alpha;
@@ -494,6 +499,17 @@ int splitk_count(int64_t m, int64_t n, int64_t k) {
   sp = std::min<int64_t>(sp, k_pad / 512);
   if (m * n * sp > ((int64_t)1 << 27)) sp = std::max<int64_t>(1, ((int64_t)1 << 27) / (m * n));
   return (int)std::max<int64_t>(sp, 1);
+}
+
+// status word for timeouts of stand-alone products (allocated once)
+int* standalone_status() {
+  static int* d = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    if (cudaMalloc(&d, sizeof(int) * kStatusWords) == cudaSuccess) cudaMemset(d, 0, sizeof(int) * kStatusWords);
+    else d = nullptr;
+  });
+  return d;
 }
 
 size_t smem_bytes(int s) {
@@ -591,7 +607,7 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
     EVD_CUDA_TRY(cudaGetLastError());
   }
   MmaArgs a;
-  a.SA = SA; a.SB = SB; a.nkb = p.k_pad / OZ_KS;
+  a.SA = SA; a.SB = SB; a.nkb = p.k_pad / OZ_KS; a.nkb_b = a.nkb; a.c_skip = 0;
   a.m = g.m; a.n = g.n; a.s = slices; a.nst = (int)(p.k_pad / OZ_KS);
   uint32_t cols = 64;
   while (cols < (uint32_t)(slices * OZ_BN)) cols <<= 1;
@@ -608,12 +624,8 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
   }
   const int zsplits = (int)ceil_div(a.nst, a.stages_per_split);
   a.part = (zsplits > 1) ? part : nullptr;
-  static int* d_dummy_status = nullptr;  // status word for timeouts of standalone products
-  if (!g.status && !d_dummy_status) {
-    if (cudaMalloc(&d_dummy_status, sizeof(int) * kStatusWords) != cudaSuccess) return EVD_ERR_OOM;
-    cudaMemset(d_dummy_status, 0, sizeof(int) * kStatusWords);
-  }
-  a.st = g.status ? g.status : d_dummy_status;
+  a.st = g.status ? g.status : standalone_status();
+  if (!a.st) return EVD_ERR_OOM;
   const size_t smem = smem_bytes(slices);
   {
     const evd_status_t st = ensure_dynamic_smem(mma_kernel(slices), smem_bytes(OZ_MAXS));
@@ -638,6 +650,136 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
 
 evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes, cudaStream_t s) {
   return ozaki_gemm_batched(g, Batch(), slices, scratch, scratch_bytes, s);
+}
+
+// ------------------------------------------------------------------ presplit operand
+size_t ozaki_presplit_bytes(int64_t m, int slices) {
+  const Pads p = pads(m, OZ_BN, m);
+  Carver c(nullptr);
+  c.take<__nv_bfloat16>((size_t)slices * p.m_pad * p.k_pad);
+  c.take<int>((size_t)p.m_pad);
+  c.take<int>((size_t)p.m_pad);
+  return c.off + 256;
+}
+
+evd_status_t ozaki_presplit_sym(const double* A, int64_t lda, int64_t m, int slices, void* buf, size_t bytes,
+                                const char* tag, SplitOperand* out, cudaStream_t s) {
+  if (slices < 1 || slices > OZ_MAXS || m < 1 || m > ((int64_t)1 << 17) || !out) return EVD_ERR_INVALID_ARG;
+  if (!buf || bytes < ozaki_presplit_bytes(m, slices)) return ws_fail(tag, bytes, ozaki_presplit_bytes(m, slices));
+  const Pads p = pads(m, OZ_BN, m);
+  Carver c(buf);
+  SplitOperand o;
+  o.S = c.take<__nv_bfloat16>((size_t)slices * p.m_pad * p.k_pad);
+  int* exb = c.take<int>((size_t)p.m_pad);
+  o.e = c.take<int>((size_t)p.m_pad);
+  o.rows = m; o.rows_pad = p.m_pad; o.K_pad = p.k_pad; o.slices = slices;
+  o.bytes = c.off + 256;
+  View va;
+  va.p = A; va.ld = lda; va.rows = m; va.K = m; va.mode = 2;
+  {
+    StatScope sc(tag, s, 0.0, 8.0 * (double)m * (double)m * 2.0 + 2.0 * slices * (double)p.m_pad * p.k_pad,
+                 "tc_split_prep");
+    EVD_CUDA_TRY(cudaMemsetAsync(exb, 0, sizeof(int) * p.m_pad, s));
+    const int64_t kspan = 1024;
+    dim3 blk(32, 8);
+    k_row_exponent<<<dim3((unsigned)ceil_div(m, 32), (unsigned)ceil_div(m, kspan)), blk, 0, s>>>(va, exb, kspan); count_launch();
+    k_split<<<dim3((unsigned)(p.m_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(va, exb, o.e, slices, p.m_pad,
+                                                                                   p.k_pad, o.S, OZ_BM); count_launch();
+    EVD_CUDA_TRY(cudaGetLastError());
+  }
+  *out = o;
+  return EVD_OK;
+}
+
+size_t ozaki_presplit_gemm_bytes(int64_t m, int64_t n, int slices) {
+  // B's slices and scales plus the split-K partials, for any offset (K <= m + OZ_BM)
+  const int64_t kp = m + OZ_BM;
+  const Pads p = pads(kp, n, kp);
+  Carver c(nullptr);
+  c.take<__nv_bfloat16>((size_t)slices * p.n_pad * p.k_pad);
+  c.take<int>((size_t)p.n_pad);
+  c.take<int>((size_t)p.n_pad);
+  c.take<double>((size_t)splitk_count(kp, n, kp) * m * n);
+  return c.off + 256;
+}
+
+evd_status_t ozaki_gemm_presplit(const Gemm& g, const SplitOperand& sa, int64_t off, void* scratch,
+                                 size_t scratch_bytes, cudaStream_t s) {
+  const int slices = sa.slices;
+  if (g.ta != 'N' || g.lower || g.m != g.k || off < 0 || off % OZ_KS != 0 || off + g.m != sa.rows || g.n < 1)
+    return EVD_ERR_INVALID_ARG;
+  // the product starts on the row tile below `off`: its first e rows (and K-elements)
+  // are computed against zero rows of B and not stored
+  const int64_t off0 = off / OZ_BM * OZ_BM, e = off - off0;
+  const int64_t mp = g.m + e, kp = g.k + e;
+  const Pads p = pads(mp, g.n, kp);
+  if (off0 + p.m_pad > sa.rows_pad || off0 + p.k_pad > sa.K_pad) return EVD_ERR_INVALID_ARG;
+  Carver c(scratch);
+  __nv_bfloat16* SB = c.take<__nv_bfloat16>((size_t)slices * p.n_pad * p.k_pad);
+  int* exB = c.take<int>((size_t)p.n_pad);
+  int* eB = c.take<int>((size_t)p.n_pad);
+  const size_t base = c.off + 256;
+  if (!scratch || scratch_bytes < base) return ws_fail(g.tag ? g.tag : "split product", scratch_bytes, base);
+  int splits = splitk_count(mp, g.n, kp);
+  while (splits > 1 && base + (size_t)splits * g.m * g.n * sizeof(double) > scratch_bytes) --splits;
+  double* part = c.take<double>(splits > 1 ? (size_t)splits * g.m * g.n : 0);
+  View vb;
+  vb.p = g.B; vb.ld = g.ldb; vb.rows = g.n; vb.K = kp; vb.koff = e;
+  vb.mode = (g.tb == 'N') ? 1 : 0;
+  {
+    StatScope sc(g.tag ? g.tag : "gemm", s, 0.0, 8.0 * (double)g.n * (double)g.k * 2.0 + 2.0 * slices * (double)p.n_pad * p.k_pad,
+                 "tc_split_prep");
+    dim3 blk(32, 8);
+    if (p.k_pad <= 512) {
+      const evd_status_t st = ensure_dynamic_smem((const void*)k_split_fused, 32 * (512 + 1) * sizeof(double));
+      if (st != EVD_OK) return st;
+      View va = vb;  // unused: every block takes B
+      k_split_fused<<<dim3((unsigned)(p.n_pad / 32), 1u), 256, 32 * (p.k_pad + 1) * sizeof(double), s>>>(
+          va, eB, SB, p.n_pad, vb, eB, SB, p.n_pad, 0, slices, p.k_pad); count_launch();
+    } else {
+      EVD_CUDA_TRY(cudaMemsetAsync(exB, 0, sizeof(int) * p.n_pad, s));
+      const int64_t kspan = 1024;
+      k_row_exponent<<<dim3((unsigned)ceil_div(g.n, 32), (unsigned)ceil_div(kp, kspan)), blk, 0, s>>>(vb, exB, kspan); count_launch();
+      k_split<<<dim3((unsigned)(p.n_pad / 32), (unsigned)(p.k_pad / 32)), blk, 0, s>>>(vb, exB, eB, slices, p.n_pad,
+                                                                                     p.k_pad, SB, OZ_BN); count_launch();
+    }
+    EVD_CUDA_TRY(cudaGetLastError());
+  }
+  MmaArgs a;
+  a.SA = sa.S + (size_t)((off0 / OZ_BM) * (sa.K_pad / OZ_KS) + off0 / OZ_KS) * slices * (OZ_BM * OZ_KS);
+  a.SB = SB;
+  a.nkb = sa.K_pad / OZ_KS; a.nkb_b = p.k_pad / OZ_KS; a.c_skip = e;
+  a.m = mp; a.n = g.n; a.s = slices; a.nst = (int)(p.k_pad / OZ_KS);
+  uint32_t cols = 64;
+  while (cols < (uint32_t)(slices * OZ_BN)) cols <<= 1;
+  a.tmem_cols = cols;
+  a.ea = sa.e + off0; a.eb = eB; a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha; a.beta = g.beta;
+  a.lower = 0; a.batched = 0; a.bm_pad = p.m_pad; a.bn_pad = p.n_pad; a.sC = 0; a.m_first = -1;
+  a.stages_per_split = (int)ceil_div(ceil_div(a.nst, splits), OZ_PERIOD) * OZ_PERIOD;
+  const int zsplits = (int)ceil_div(a.nst, a.stages_per_split);
+  a.part = (zsplits > 1) ? part : nullptr;
+  a.st = g.status ? g.status : standalone_status();
+  if (!a.st) return EVD_ERR_OOM;
+  {
+    const evd_status_t st = ensure_dynamic_smem(mma_kernel(slices), smem_bytes(OZ_MAXS));
+    if (st != EVD_OK) return st;
+  }
+  dim3 grid((unsigned)(p.m_pad / OZ_BM), (unsigned)(p.n_pad / OZ_BN), (unsigned)zsplits);
+  if (grid.y > 65535) return EVD_ERR_INVALID_ARG;
+  StatScope sc(g.tag ? g.tag : "gemm", s, 2.0 * (double)mp * g.n * kp * (double)(slices * (slices + 1) / 2), 0.0,
+               "tc_split");
+  void* kargs[] = {&a};
+  EVD_CUDA_TRY(cudaLaunchKernel(mma_kernel(slices), grid, dim3(OZ_THREADS), kargs, smem_bytes(slices), s)); count_launch();
+  EVD_CUDA_TRY(cudaGetLastError());
+  if (zsplits > 1) {
+    for (int64_t j0 = 0; j0 < g.n; j0 += 65535) {
+      const int64_t cols2 = std::min<int64_t>(g.n - j0, 65535);
+      k_splitk_reduce<<<dim3((unsigned)std::min<int64_t>(ceil_div(g.m, 256), 16), (unsigned)cols2), 256, 0, s>>>(
+          part + j0 * g.m, zsplits, g.m, g.n, g.alpha, g.beta, g.C + j0 * g.ldc, g.ldc, 0); count_launch();
+    }
+    EVD_CUDA_TRY(cudaGetLastError());
+  }
+  return EVD_OK;
 }
 
 }  // namespace evd

@@ -5,6 +5,8 @@
 // converted to FP64 once per output element.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "evd_internal.h"
 
 namespace evd {
@@ -26,5 +28,26 @@ evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void
                                 cudaStream_t s);
 bool ozaki_eligible(const Gemm& g);
 evd_status_t ozaki_gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes, cudaStream_t s);
+
+// An A operand split once and used by several products: the slices of a
+// symmetric m x m matrix (lower triangle stored) in 128-row tiles, K padded to 32,
+// with its per-row scales.  The double-blocked SBR's Z products of one block read
+// principal submatrices of the same stale trailing matrix (Sec. 4.1).
+struct SplitOperand {
+  __nv_bfloat16* S = nullptr;
+  int* e = nullptr;
+  int64_t rows = 0, rows_pad = 0, K_pad = 0;
+  int slices = 0;
+  size_t bytes = 0;  // of the buffer it occupies
+};
+size_t ozaki_presplit_bytes(int64_t m, int slices);
+evd_status_t ozaki_presplit_sym(const double* A, int64_t lda, int64_t m, int slices, void* buf, size_t bytes,
+                                const char* tag, SplitOperand* out, cudaStream_t s);
+// C = alpha A(off:, off:) op(B) + beta C with A the presplit operand (g.A ignored;
+// g.m == g.k == rows - off, off a multiple of 16, g.ta == 'N').  The row scales
+// are those of the whole operand's rows.  Scratch: ozaki_presplit_gemm_bytes.
+size_t ozaki_presplit_gemm_bytes(int64_t m, int64_t n, int slices);
+evd_status_t ozaki_gemm_presplit(const Gemm& g, const SplitOperand& sa, int64_t off, void* scratch,
+                                 size_t scratch_bytes, cudaStream_t s);
 
 }  // namespace evd

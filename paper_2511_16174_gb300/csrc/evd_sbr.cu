@@ -17,6 +17,7 @@
 
 #include "device_util.cuh"
 #include "evd_internal.h"
+#include "evd_ozaki.h"
 
 namespace evd {
 
@@ -369,15 +370,47 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
   if (maxG < 1) return EVD_ERR_CUDA;
   const int maxG_smem = max_coresident_blocks((const void*)k_panel_qr_smem, PQ_NT, 200 * 1024);
   const int64_t ldz = n;  // leading dimension of VZ, ZV
+  // scratch of the products; during a block with a presplit trailing matrix, what
+  // follows the presplit
+  char* gws = static_cast<char*>(w.gemm_ws);
+  size_t gws_bytes = w.gemm_ws_bytes;
   auto gemm_tag = [&](Gemm g, const char* tag, bool tc) {
     g.status = pc.status;
     g.tag = tag;
-    return gemm(g, tc ? pc.slices : 0, w.gemm_ws, w.gemm_ws_bytes, s);
+    return gemm(g, tc ? pc.slices : 0, gws, gws_bytes, s);
   };
+  // The Z products of one block all read principal submatrices of the block's
+  // stale trailing matrix A(r0:, r0:): with more than one panel per block it is
+  // split into slices once, at the block's start, when the scratch holds it next to
+  // the largest product a panel runs.
+  const size_t panel_scratch =
+      std::max({gemm_scratch_bytes(n, b, 2 * (int64_t)pc.nb, pc.slices), gemm_scratch_bytes(2 * (int64_t)pc.nb, b, n, pc.slices),
+                pc.slices > 0 ? ozaki_presplit_gemm_bytes(n, b, pc.slices) : (size_t)0});
   int64_t p = 0;
   bool done = false;
   while (!done) {
     int acc = 0;  // columns of V (and of Z) accumulated in this block
+    SplitOperand pre;
+    bool use_pre = false;
+    gws = static_cast<char*>(w.gemm_ws);
+    gws_bytes = w.gemm_ws_bytes;
+    {
+      const int64_t r0b = p * b + b, mb = n - r0b;
+      if (nbp > 1 && b % 16 == 0 && pc.slices > 0 && mb >= 2 * b && mb <= ((int64_t)1 << 17)) {
+        Gemm probe;
+        probe.m = mb; probe.n = b; probe.k = mb;
+        const size_t need = align_up(ozaki_presplit_bytes(mb, pc.slices), 256);
+        if (ozaki_eligible(probe) && need + panel_scratch <= w.gemm_ws_bytes) {
+          const evd_status_t st = ozaki_presplit_sym(A + r0b + r0b * lda, lda, mb, pc.slices, w.gemm_ws, need, "sbr_z",
+                                                     &pre, s);
+          if (st != EVD_OK) return st;
+          use_pre = true;
+          gws = static_cast<char*>(w.gemm_ws) + need;
+          gws_bytes = w.gemm_ws_bytes - need;
+        }
+      }
+    }
+    const int64_t r0_block = p * b + b;
     for (int q = 0; q < nbp; ++q) {
       const int64_t c0 = p * b, r0 = c0 + b, m = n - r0;
       if (m < 2) { done = true; break; }
@@ -426,7 +459,14 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
         Gemm g;
         g.m = m; g.n = kb; g.k = m; g.A = A2; g.lda = lda; g.a_sym_lower = true;
         g.B = w.W; g.ldb = n; g.C = w.Y; g.ldc = n; g.alpha = 1.0; g.beta = 0.0;
-        st = gemm_tag(g, "sbr_z", true);
+        if (use_pre && ozaki_eligible(g) && r0 - r0_block + m == pre.rows) {
+          g.a_sym_lower = false;  // the presplit holds the mirrored matrix
+          g.status = pc.status;
+          g.tag = "sbr_z";
+          st = ozaki_gemm_presplit(g, pre, r0 - r0_block, gws, gws_bytes, s);
+        } else {
+          st = gemm_tag(g, "sbr_z", true);
+        }
         if (st != EVD_OK) return st;
       }
       if (acc > 0) {
@@ -476,7 +516,10 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
       EVD_CUDA_TRY(cudaGetLastError());
       ++p;
     }
-    // ---- block end: trailing lower triangle from column c = p b
+    // ---- block end: trailing lower triangle from column c = p b (the presplit is
+    // stale from here on; the whole scratch is free again)
+    gws = static_cast<char*>(w.gemm_ws);
+    gws_bytes = w.gemm_ws_bytes;
     const int64_t c = p * b;
     if (acc > 0 && c < n) {
       Gemm g;

@@ -182,19 +182,26 @@ __global__ void k_dc_prepare(const MergeDesc* md, const double* d, const double*
 //   kind[t] = 0 nondeflated / 1 deflated; nd list (ascending) in ndl[off..off+k);
 //   deflated list in dfl[off .. off+m-k); rotations (p, j, c, s) in rot arrays.
 // Per merge: k, number of rotations.
+// The merged block's columns are zero outside their half (Q1 rows 0..n1-1, Q2 rows
+// n1..m-1) unless a deflation rotation mixed the two halves.  Each nondeflated
+// column i gets a group (1: top rows only, 3: both, 2: bottom rows only) and its
+// position pos[off+i] in the order [top | both | bottom] (ascending within a
+// group), with grp[2 t] = #top, grp[2 t + 1] = #both: the product Qn U then splits
+// into a top and a bottom product over column ranges of that order.
 __global__ void k_dc_deflate(const MergeDesc* md, int count, double* ds, double* zs, const double* rho_in,
-                             const double* tol_in, int* ndl, int* dfl, int* rotp, int* rotj, double* rotc,
-                             double* rots, int* kout, int* nrot_out) {
+                             const double* tol_in, const int* perm, int* ndl, int* dfl, int* rotp, int* rotj,
+                             double* rotc, double* rots, int* kout, int* nrot_out, int* pos, int* grp) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const MergeDesc M = md[t];
   const int64_t off = M.off, m = M.n1 + M.n2;
   const double rho = rho_in[t], tol = tol_in[t];
   int k = 0, nd_df = 0, nr = 0;
-  int pj = -1;
+  int pj = -1, ptype = 0;
   for (int j = 0; j < m; ++j) {
     if (rho * fabs(zs[off + j]) <= tol) { dfl[off + nd_df++] = j; continue; }
-    if (pj < 0) { pj = j; continue; }
+    const int bj = (perm[off + j] < M.n1) ? 1 : 2;
+    if (pj < 0) { pj = j; ptype = bj; continue; }
     double s = zs[off + pj], c = zs[off + j];
     double r = hypot(s, c);
     double cc = c / r, ss = s / r;
@@ -208,12 +215,30 @@ __global__ void k_dc_deflate(const MergeDesc* md, int count, double* ds, double*
       rotp[off + nr] = pj; rotj[off + nr] = j; rotc[off + nr] = cc; rots[off + nr] = ss; ++nr;
       dfl[off + nd_df++] = pj;
       pj = j;
+      ptype |= bj;  // column j now holds a combination of both
     } else {
+      pos[off + k] = ptype;
       ndl[off + k++] = pj;
       pj = j;
+      ptype = bj;
     }
   }
-  if (pj >= 0) ndl[off + k++] = pj;
+  if (pj >= 0) {
+    pos[off + k] = ptype;
+    ndl[off + k++] = pj;
+  }
+  int c1 = 0, c2 = 0;
+  for (int i = 0; i < k; ++i) {
+    c1 += (pos[off + i] == 1);
+    c2 += (pos[off + i] == 3);
+  }
+  int a1 = 0, a2 = c1, a3 = c1 + c2;
+  for (int i = 0; i < k; ++i) {
+    const int g = pos[off + i];
+    pos[off + i] = (g == 1) ? a1++ : (g == 3) ? a2++ : a3++;
+  }
+  grp[2 * t] = c1;
+  grp[2 * t + 1] = c2;
   kout[t] = k;
   nrot_out[t] = nr;
 }
@@ -249,8 +274,8 @@ __global__ void k_dc_rotate(const MergeDesc* md, const int* nrot, const int* rot
 }
 
 // Gather the nondeflated poles and z: dl[i] = ds[ndl[i]], zl[i] = zs[ndl[i]],
-// and the nondeflated columns Qn(:, i) = Qt(:, ndl[i]).
-__global__ void k_dc_gather_nd(const MergeDesc* md, const int* kk, const int* ndl, const double* ds,
+// and the nondeflated columns Qn(:, pos[i]) = Qt(:, ndl[i]) (grouped order).
+__global__ void k_dc_gather_nd(const MergeDesc* md, const int* kk, const int* ndl, const int* pos, const double* ds,
                                const double* zs, double* dl, double* zl, const double* Qt, int64_t ldt, double* Qn) {
   const MergeDesc M = md[blockIdx.z];
   const int64_t off = M.off, m = M.n1 + M.n2;
@@ -260,7 +285,7 @@ __global__ void k_dc_gather_nd(const MergeDesc* md, const int* kk, const int* nd
   int64_t src = ndl[off + i];
   if (blockIdx.x == 0 && threadIdx.x == 0) { dl[off + i] = ds[off + src]; zl[off + i] = zs[off + src]; }
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
-    Qn[(off + r) + (off + i) * ldt] = Qt[(off + r) + (off + src) * ldt];
+    Qn[(off + r) + (off + pos[off + i]) * ldt] = Qt[(off + r) + (off + src) * ldt];
 }
 
 // ---------------------------------------------------------------- secular equation
@@ -377,8 +402,9 @@ __global__ void k_dc_lowner(const MergeDesc* md, const int* kk, const double* dl
 
 // Eigenvector i of D + rho zhat zhat^T: u(j) = zhat_j / (d_j - lambda_i), normalised.
 // Written as column i of the k x k matrix U at the merge's diagonal block (ld ldu).
+// Column i of U (root i), its rows in the grouped order of the poles (pos).
 __global__ void k_dc_vectors(const MergeDesc* md, const int* kk, const double* dl, const int* org,
-                             const double* tau, const double* zh, double* U, int64_t ldu) {
+                             const double* tau, const double* zh, const int* pos, double* U, int64_t ldu) {
   const MergeDesc M = md[blockIdx.y];
   const int k = kk[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -392,7 +418,7 @@ __global__ void k_dc_vectors(const MergeDesc* md, const int* kk, const double* d
   }
   const double inv = 1.0 / sqrt(ss);
   double* col = U + off + (off + i) * ldu;
-  for (int j = 0; j < k; ++j) col[j] = zh[off + j] / ((dl[off + j] - dorg) - ti) * inv;
+  for (int j = 0; j < k; ++j) col[pos[off + j]] = zh[off + j] / ((dl[off + j] - dorg) - ti) * inv;
 }
 
 __device__ __forceinline__ long long order_key(double x) {
@@ -496,6 +522,7 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
   int* rotj = w.ivec + 4 * n;
   int* org = w.ivec + 5 * n;
   int* rank = w.ivec + 6 * n;
+  int* pos = w.ivec + 7 * n;
   // merge descriptors and per-merge scalars
   std::vector<MergeDesc> all;
   std::vector<size_t> lvl_start;
@@ -515,6 +542,7 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
   double* d_tol = reinterpret_cast<double*>(carve(sizeof(double) * (nmerge + 1)));
   int* d_k = reinterpret_cast<int*>(carve(sizeof(int) * (nmerge + 1)));
   int* d_nrot = reinterpret_cast<int*>(carve(sizeof(int) * (nmerge + 1)));
+  int* d_grp = reinterpret_cast<int*>(carve(sizeof(int) * 2 * (nmerge + 1)));
   if (mb > ((size_t)24 * n + 1024) * sizeof(int)) return ws_fail("dc merge descriptors", ((size_t)24 * n + 1024) * sizeof(int), mb);
   if (nmerge) EVD_CUDA_TRY(cudaMemcpyAsync(d_md, all.data(), sizeof(MergeDesc) * nmerge, cudaMemcpyHostToDevice, s));
   EVD_CUDA_TRY(cudaMemcpyAsync(d_loff, loff.data(), sizeof(int64_t) * nleaves, cudaMemcpyHostToDevice, s));
@@ -531,7 +559,7 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
                                                                      pc.status); count_launch();
   }
   EVD_CUDA_TRY(cudaGetLastError());
-  std::vector<int> hk(nmerge + 1);
+  std::vector<int> hk(nmerge + 1), hg(2 * (nmerge + 1));
   for (size_t L = 0; L + 1 < lvl_start.size(); ++L) {
     const size_t b0 = lvl_start[L], cnt = lvl_start[L + 1] - b0;
     if (cnt == 0) continue;
@@ -541,8 +569,9 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
     const unsigned rx = (unsigned)std::min<int64_t>(ceil_div(mmax, 256), 8);
     { StatScope sc("dc_merge", s);
     k_dc_prepare<<<(unsigned)cnt, 256, 0, s>>>(md, d, e, Q, ldq, ds, zs, perm, d_rho + b0, d_tol + b0); count_launch();
-    k_dc_deflate<<<(unsigned)ceil_div(cnt, 64), 64, 0, s>>>(md, (int)cnt, ds, zs, d_rho + b0, d_tol + b0, ndl, dfl,
-                                                            rotp, rotj, rotc, rots, d_k + b0, d_nrot + b0); count_launch();
+    k_dc_deflate<<<(unsigned)ceil_div(cnt, 64), 64, 0, s>>>(md, (int)cnt, ds, zs, d_rho + b0, d_tol + b0, perm, ndl,
+                                                            dfl, rotp, rotj, rotc, rots, d_k + b0, d_nrot + b0, pos,
+                                                            d_grp + 2 * b0); count_launch();
     k_dc_gather<<<dim3(rx, (unsigned)mmax, (unsigned)cnt), 256, 0, s>>>(md, perm, Q, ldq, w.Qtmp, n); count_launch();
     k_dc_rotate<<<dim3((unsigned)ceil_div(mmax, 128), (unsigned)cnt), 128, 0, s>>>(md, d_nrot + b0, rotp, rotj, rotc,
                                                                                  rots, w.Qtmp, n); count_launch();
@@ -550,35 +579,43 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
     }
     // the number of nondeflated roots sizes the products: read it on the host
     EVD_CUDA_TRY(cudaMemcpyAsync(hk.data(), d_k + b0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+    EVD_CUDA_TRY(cudaMemcpyAsync(hg.data(), d_grp + 2 * b0, sizeof(int) * 2 * cnt, cudaMemcpyDeviceToHost, s));
     EVD_CUDA_TRY(cudaStreamSynchronize(s));
     int kmax = 0;
     for (size_t q = 0; q < cnt; ++q) kmax = std::max(kmax, hk[q]);
     if (kmax > 0) {
-      k_dc_gather_nd<<<dim3(rx, (unsigned)kmax, (unsigned)cnt), 256, 0, s>>>(md, d_k + b0, ndl, ds, zs, dl, zl,
+      k_dc_gather_nd<<<dim3(rx, (unsigned)kmax, (unsigned)cnt), 256, 0, s>>>(md, d_k + b0, ndl, pos, ds, zs, dl, zl,
                                                                              w.Qtmp, n, w.Qn); count_launch();
       const unsigned kx = (unsigned)ceil_div(kmax, 128);
       { StatScope sc("dc_secular", s);
       k_dc_secular<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, zl, d_rho + b0, org, tau, pc.status); count_launch();
       k_dc_lowner<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, zl, d_rho + b0, org, tau, zh); count_launch();
-      k_dc_vectors<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, org, tau, zh, w.Umat, n); count_launch();
+      k_dc_vectors<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, org, tau, zh, pos, w.Umat, n); count_launch();
       EVD_CUDA_TRY(cudaGetLastError());
       }
-      // X = Qn U into the first k columns of the block of Q (the block is free now)
+      // X = Qn U into the first k columns of the block of Q (the block is free now),
+      // as X(0:n1, :) = Qn(0:n1, 0:c1+c2) U(0:c1+c2, :) and
+      //    X(n1:m, :) = Qn(n1:m, c1:k)     U(c1:k, :)
       for (size_t q = 0; q < cnt; ++q) {
         const int k = hk[q];
         if (k == 0) continue;
         const MergeDesc& M = all[b0 + q];
-        const int64_t m = M.n1 + M.n2, off = M.off;
-        Gemm g;
-        g.tag = "dc_merge_gemm";
-        g.status = pc.status;
-        g.m = m; g.n = k; g.k = k;
-        g.A = w.Qn + off + off * n; g.lda = n;
-        g.B = w.Umat + off + off * n; g.ldb = n;
-        g.C = Q + off + off * ldq; g.ldc = ldq;
-        g.alpha = 1.0; g.beta = 0.0;
-        evd_status_t st = gemm(g, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
-        if (st != EVD_OK) return st;
+        const int64_t off = M.off, n1 = M.n1, n2 = M.n2;
+        const int c1 = hg[2 * q], c2 = hg[2 * q + 1];
+        for (int half = 0; half < 2; ++half) {
+          const int64_t r0 = half ? n1 : 0, rows = half ? n2 : n1;
+          const int64_t j0 = half ? c1 : 0, kk = half ? (int64_t)k - c1 : (int64_t)c1 + c2;
+          Gemm g;
+          g.tag = "dc_merge_gemm";
+          g.status = pc.status;
+          g.m = rows; g.n = k; g.k = kk;
+          g.A = w.Qn + (off + r0) + (off + j0) * n; g.lda = n;
+          g.B = w.Umat + (off + j0) + off * n; g.ldb = n;
+          g.C = Q + (off + r0) + off * ldq; g.ldc = ldq;
+          g.alpha = 1.0; g.beta = 0.0;
+          evd_status_t st = gemm(g, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
+          if (st != EVD_OK) return st;
+        }
       }
     }
     StatScope sc2("dc_merge", s);

@@ -141,6 +141,36 @@ def test_tridiag_solve_deflation_heavy(evd):
     assert np.linalg.norm(T @ Q - Q * to_host(d)) / (n * np.linalg.norm(T)) <= 10 * U
 
 
+def test_tridiag_solve_glued_copies(evd):
+    """16 copies of one tridiagonal block glued by 1e-9: every eigenvalue of the
+    block appears 16 times, so the merges deflate by rotations that mix columns of
+    their two halves; the top merges are large enough for the tensor-core product."""
+    n, nb_ = 2048, 128
+    r = inputs.rng(9100)
+    d0 = r.standard_normal(nb_)
+    e0 = r.standard_normal(nb_ - 1)
+    dd = np.tile(d0, n // nb_)
+    ee = np.zeros(n - 1)
+    for blk in range(n // nb_):
+        ee[blk * nb_: blk * nb_ + nb_ - 1] = e0
+    ee[nb_ - 1::nb_] = 1e-9
+    w_ref, _ = oracle.steql(dd, ee, None)
+    plan = evd.Plan(n, job="V", b=2, nb=2)
+    ws = plan.workspace()
+    d = torch.tensor(dd, device="cuda")
+    e = torch.zeros(n, dtype=torch.float64, device="cuda")
+    e[: n - 1] = torch.tensor(ee, device="cuda")
+    Qd = evd.empty_colmajor(n, n)
+    plan.tridiag_solve(d, e, Qd, ws)
+    plan.check("dc")
+    Q = to_host(Qd)
+    T = np.diag(dd) + np.diag(ee, 1) + np.diag(ee, -1)
+    tn = norm2(T)
+    assert np.max(np.abs(to_host(d) - np.sort(w_ref))) <= 10 * n * U * tn
+    assert np.max(np.abs(Q.T @ Q - np.eye(n))) <= 10 * n * U
+    assert np.linalg.norm(T @ Q - Q * to_host(d)) / (n * np.linalg.norm(T)) <= 10 * U
+
+
 def _check_full(A, w, Q, w_ref=None):
     n = A.shape[0]
     acc = oracle.acceptance(n, norm2(A))

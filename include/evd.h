@@ -65,8 +65,8 @@ typedef enum { EVD_FP64 = 0, EVD_SPLIT_INT8 = 1, EVD_SPLIT_BF16 = 2 } evd_prec_t
  *   b   band half-width of SBR (Sec. 2.1.1; typical 32, Sec. 4.1).
  *   nb  outer (double-blocking) width of SBR, a multiple of b.
  *   b = nb = 0: the autotuner's cached choice (see evd_autotune), else b = 64 for
- *   n >= 4096 and 32 below, nb = 4 b for n >= 16384 and b below.  b > 0, nb = 0:
- *   nb = b.
+ *   n >= 4096 and 32 below, nb = 16 b for n >= 32768, 8 b for n >= 16384 and b
+ *   below.  b > 0, nb = 0: nb = b.
  *   stream  a cudaStream_t (passed as void*), NULL for the legacy default stream.
  * Must be called with the target device current.  Returns EVD_ERR_INVALID_ARG for
  * n < 0, lda < max(1, n), b < 0, nb < 0, b > 0 && nb % b != 0, or b > 128. */

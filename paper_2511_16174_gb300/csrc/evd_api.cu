@@ -225,7 +225,7 @@ namespace evd {
 
 // The plan's tunables.  b = nb = 0: the autotuner's cached choice (file named by
 // EVD_AUTOTUNE_CACHE) if there is one, else b = 64 for n >= 4096 and 32 below,
-// nb = 4 b for n >= 16384 and b below.  b > 0, nb = 0: nb = b.
+// nb = 16 b for n >= 32768, 8 b for n >= 16384 and b below.  b > 0, nb = 0: nb = b.
 void fill_core(PlanCore& c, int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb) {
   c.n = n;
   c.lda = lda;
@@ -238,8 +238,10 @@ void fill_core(PlanCore& c, int64_t n, int64_t lda, evd_job_t job, evd_prec_t pr
   } else {
     c.b = (b > 0) ? b : default_b(n);
     if (c.b < 2 && b == 0) c.b = 2;
-    // double blocking pays once the trailing matrix is large (fewer, wider syr2k)
-    c.nb = (nb > 0) ? nb : ((b == 0 && n >= 16384) ? 4 * c.b : c.b);
+    // double blocking pays once the trailing matrix is large (fewer, wider syr2k,
+    // one split of the stale trailing matrix per block)
+    const int dbl = (b != 0) ? 1 : (n >= 32768) ? 16 : (n >= 16384) ? 8 : 1;
+    c.nb = (nb > 0) ? nb : dbl * c.b;
   }
   // split precision: 6 slices (21 slice pairs instead of 36) leave the eigenvectors
   // accurate enough (about 1e-11 at n ~ 1e3) for two refinement steps to resolve

@@ -315,7 +315,7 @@ evd_status_t sbr_back_run(const PlanCore& pc, const double* A, const double* sbr
         Gemm gd;
         gd.m = Kp; gd.n = kb; gd.k = Kp; gd.A = w.Tblk; gd.lda = ldk; gd.B = w.Cblk; gd.ldb = ldk;
         gd.C = w.Cblk + (size_t)ldk * b; gd.ldc = ldk; gd.alpha = 1.0; gd.beta = 0.0;
-        st = pgemm(gd, 0);
+        st = pgemm(gd, pc.slices);  // the split product once Kp is large enough
         if (st != EVD_OK) return st;
         Gemm ge;
         ge.m = Kp; ge.n = kb; ge.k = kb; ge.A = gd.C; ge.lda = ldk; ge.B = w.Tblk + Kp + Kp * ldk; ge.ldb = ldk;

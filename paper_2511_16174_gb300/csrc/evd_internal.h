@@ -150,7 +150,7 @@ struct DcWork {
 evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t ldq,
                     const DcWork& w);
 
-constexpr int kSbrBackPanels = 8;  // SBR panels merged into one compact WY group in SBR-Back
+constexpr int kSbrBackPanels = 16;  // SBR panels merged into one compact WY group in SBR-Back
 struct BackWork {
   double* Tg;      // T factors of the BC reflector groups
   double* Vg;      // V of the BC reflector groups of one wave (count x h x g)

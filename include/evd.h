@@ -101,7 +101,10 @@ evd_status_t evd_tridiag_solve(evd_plan_t plan, double* d, double* e, double* Qd
 /* Stage 4 -- back transformation (Sec. 2.1.2, conventional order): on entry Q holds
  * Q_d; on exit Q = Q_s Q_b Q_d, the eigenvectors of the A given to evd_sbr.  Reads
  * the SBR vectors from the A passed to evd_sbr (still needed: pass it again) and
- * the BC vectors from ws. */
+ * the BC vectors from ws.  With b = 64 and a Q whose base address is 16-byte aligned
+ * and ldq even, BC-Back runs the fused wave kernel (Q is held in int64 fixed point in
+ * place while it runs); otherwise it runs the batched split products.  Both give
+ * FP64-level results. */
 evd_status_t evd_back_transform(evd_plan_t plan, const double* A_reduced, void* ws, double* Q,
                                 int64_t ldq);
 

@@ -133,21 +133,28 @@ class ClockSampler:
 
 def run_oracle_sample(target_s=15.0):
     """Time the CPU oracle (one-stage tridiagonalization + implicit QL with
-    vectors) on a bounded sample; returns (tflops, n_sample, seconds, cores)."""
+    vectors) on a bounded sample of the workload: the same construction (A = Q
+    Lambda Q^T, Lambda uniform in [-1, 1]) at the size ns that takes about target_s
+    seconds.  Returns (tflops, ns, seconds, cores)."""
     import oracle
     from paper_2511_16174_gb300 import inputs
     n0 = 768
-    A = inputs.goe(n0, 1)
+    A = inputs.qlq(inputs.spectrum_uniform(n0, 1), 2)
     t = time.perf_counter()
     oracle.eigh(A, want_vectors=True)
     t0 = time.perf_counter() - t
     ns = int(n0 * (target_s / max(t0, 1e-3)) ** (1.0 / 3.0))
     ns = max(512, min(4096, ns // 64 * 64))
-    A = inputs.goe(ns, 2)
+    A = inputs.qlq(inputs.spectrum_uniform(ns, 3), 4)
     t = time.perf_counter()
     oracle.eigh(A, want_vectors=True)
     ts = time.perf_counter() - t
     return nominal_flops(ns) / ts / 1e12, ns, ts, oracle.num_threads()
+
+
+def sample_text(ns, secs):
+    return (f"one-stage Householder + implicit QL with vectors on the same construction at n={ns} "
+            f"(A = Q Lambda Q^T, Lambda uniform [-1,1]), {secs:.1f} s per solve; flops counted as 4n^3/3+2n^3")
 
 
 def dist_setup():
@@ -173,10 +180,11 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(n, args.prec), "n": n, "job": "V", "prec": args.prec},
+        "config": {"workload": f"CPU oracle on a bounded sample of the n={n} workload: each step one solve at "
+                               f"n={ns} of the same construction, TFLOP/s of that sample (not an n={n} solve)",
+                   "n": n, "sample_n": ns, "job": "V", "prec": args.prec},
         "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": f"one-stage Householder + implicit QL with vectors at n={ns} (GOE input), "
-                                   f"{float(np.mean(times)):.1f} s per solve; flops counted as 4n^3/3+2n^3"},
+                         "sample": sample_text(ns, float(np.mean(times)))},
         "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -201,16 +209,38 @@ def ours(args):
     else:
         A0 = evd.as_colmajor(inputs.qlq_device(lam, seed))
     torch.cuda.synchronize()
+    # The step's input lives in pinned host memory; A is symmetric, so the row-major
+    # host copy of the column-major device matrix holds the same values.
+    Ah = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    Ah.copy_(A0.t())
+    del A0
+    torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
-    plan = evd.Plan(n, job="V", prec=args.prec, b=args.b, nb=args.nb, stream=stream)
+    options = {"refine_iters": args.refine_iters} if args.refine_iters is not None else None
+    plan = evd.Plan(n, job="V", prec=args.prec, b=args.b, nb=args.nb, stream=stream, options=options)
     ws = plan.workspace()
     Aw = evd.empty_colmajor(n, n)
     w = torch.empty(n, dtype=torch.float64, device="cuda")
     Q = evd.empty_colmajor(n, n)
+    wh = torch.empty(n, dtype=torch.float64).pin_memory()
+    Qh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    Aw_rm = Aw.t()  # row-major view of the column-major buffer
 
-    def step():
-        Aw.copy_(A0)
+    def step(ev=None):
+        """One step through the public API: host -> device copy of A, the solve,
+        device -> host copy of w and Q (the row-major host Qh holds Q^T)."""
+        if ev:
+            ev[0].record(stream)
+        Aw_rm.copy_(Ah, non_blocking=True)
+        if ev:
+            ev[1].record(stream)
         plan.syevd(Aw, w, Q, ws)
+        if ev:
+            ev[2].record(stream)
+        wh.copy_(w, non_blocking=True)
+        Qh.copy_(Q.t(), non_blocking=True)
+        if ev:
+            ev[3].record(stream)
 
     for i in range(args.warmup):
         step()
@@ -223,16 +253,13 @@ def ours(args):
     clocks.start()
     evd.stats_reset()
     evd.stats_enable(not args.no_stats)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     torch.cuda.synchronize()
     if ws_ > 1:
         dist.barrier()
     torch.cuda.nvtx.range_push("timed_steps")  # ncu --nvtx-include "timed_steps/" takes exactly these launches
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if ws_ > 1:
@@ -240,17 +267,27 @@ def ours(args):
     evd.stats_enable(False)
     launches = evd.launch_count()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
     plan.check("timed solves")
+    # value: the solves alone (inputs resident in HBM); e2e: the whole steps
+    ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    ems = evs[0][0].elapsed_time(evs[-1][3]) / args.steps
+    h2d_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    d2h_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
     st = evd.stats()
     if ws_ > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        t = torch.tensor([ms, ems], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms, ems = float(t[0].item()), float(t[1].item())
     value = nominal_flops(n) / (ms / 1e3) / 1e12 * ws_
+    e2e = {"value": nominal_flops(n) / (ems / 1e3) / 1e12 * ws_, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n + 8 * n * n,
+           "ms_per_step": ems, "h2d_ms": h2d_ms, "d2h_ms": d2h_ms}
 
-    # ---- accuracy of the last timed result (sampled columns at large n)
+    # ---- accuracy of the last timed result (sampled columns at large n); A is
+    # copied back into the solve's input buffer from the host copy
     with torch.no_grad():
+        Aw_rm.copy_(Ah)
+        A0 = Aw
         lam_t = torch.from_numpy(lam).cuda()
         dlam = float((w - lam_t).abs().max().item())
         gen = torch.Generator(device="cuda")
@@ -258,17 +295,21 @@ def ours(args):
         cols = (torch.arange(n, device="cuda") if n <= 8192
                 else torch.randperm(n, device="cuda", generator=gen)[:256])
         Qs = Q[:, cols]
-        A0s = A0
-        R = A0s @ Qs - Qs * w[cols][None, :]
+        R = A0 @ Qs - Qs * w[cols][None, :]
         O = Q.t() @ Qs
         O[cols, torch.arange(len(cols), device="cuda")] -= 1.0
         normA = float(torch.linalg.matrix_norm(A0).item())
         resid = float(torch.linalg.matrix_norm(R).item()) / (n * normA) * (n / len(cols)) ** 0.5
         orth = float(O.abs().max().item())
+        # the host copy of the result is the device result
+        host_ok = bool(torch.equal(Qh[cols.cpu()].t().contiguous(), Qs.cpu()) and torch.equal(wh, w.cpu()))
+        del R, O, Qs
     U = 2.0 ** -53
     acc = {"dlam": dlam, "dlam_bound": 10 * n * U * float(np.max(np.abs(lam))), "orth_max": orth,
            "orth_bound": 10 * n * U, "resid": resid, "resid_bound": 10 * U,
-           "columns_checked": int(len(cols))}
+           "columns_checked": int(len(cols)), "host_copy_matches": host_ok}
+    acc["within_bounds"] = bool(acc["dlam"] <= acc["dlam_bound"] and acc["orth_max"] <= acc["orth_bound"]
+                                and acc["resid"] <= acc["resid_bound"])
 
     # ---- roofline of the dominant kernel category
     # Categories are "stage/engine" for products ("/tc_split": tensor-core split
@@ -303,40 +344,10 @@ def ours(args):
         roof["share_of_step"] = dms / (ms * args.steps) if ms > 0 else None
     breakdown = {k: {"ms": v[0] / args.steps, "calls": v[3] // max(args.steps, 1)} for k, v in st.items()}
 
-    # ---- end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
-        Ah = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        Ah.copy_(A0.t())  # A is symmetric: the row-major copy holds the same values
-        wh = torch.empty(n, dtype=torch.float64).pin_memory()
-        Qh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        Aw_rm = Aw.t()  # row-major view of the column-major buffer
-
-        def e2e_step():
-            Aw_rm.copy_(Ah, non_blocking=True)
-            plan.syevd(Aw, w, Q, ws)
-            wh.copy_(w, non_blocking=True)
-            Qh.copy_(Q.t(), non_blocking=True)
-
-        torch.cuda.synchronize()  # the plan is warm from the solves above
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1) / args.steps
-        e2e = {"value": nominal_flops(n) / (ems / 1e3) / 1e12 * ws_, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n + 8 * n * n,
-               "ms_per_step": ems}
-
     cpu = None
     if rank == 0 and ws_ == 1 and not args.no_cpu:
         tf, ns, ts, cores = run_oracle_sample()
-        cpu = {"value": tf, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": f"one-stage Householder + implicit QL with vectors at n={ns} (GOE input), {ts:.1f} s; "
-                         f"flops counted as 4n^3/3+2n^3"}
+        cpu = {"value": tf, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample_text(ns, ts)}
 
     if rank == 0:
         line = {
@@ -346,6 +357,7 @@ def ours(args):
             "config": {"workload": workload_name(n, args.prec), "n": n, "job": "V", "prec": args.prec,
                        "b": plan.b, "nb": plan.nb, "seconds_per_solve": ms / 1e3,
                        "paper_tflops_4n3": 4.0 * n ** 3 / (ms / 1e3) / 1e12,
+                       "refine_iters": plan.option("refine_iters") if args.prec != "fp64" else 0,
                        "l2": "inputs larger than L2 (A is 8 n^2 bytes)", "parallelism": f"replicas{ws_}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "accuracy": acc, "stages": breakdown,
@@ -391,7 +403,7 @@ def main():
     ap.add_argument("--prec", choices=["fp64", "split_bf16"], default="fp64")
     ap.add_argument("--b", type=int, default=0)
     ap.add_argument("--nb", type=int, default=0)
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--refine-iters", type=int, default=None, help="refinement steps of the split form")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="no per-category event timing in the timed region")
     ap.add_argument("--profile", choices=["gemm", "solve"], default=None,

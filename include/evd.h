@@ -78,6 +78,35 @@ evd_status_t evd_plan_create(evd_plan_t* plan, int64_t n, int64_t lda, evd_job_t
  * solve, since later stages read what earlier stages left there. */
 evd_status_t evd_plan_workspace_size(evd_plan_t plan, size_t* bytes);
 
+/* Plan options: tunables that change how a solve runs, never what it computes
+ * beyond the stated accuracy.  Set them after evd_plan_create and before
+ * evd_plan_workspace_size and the first stage call (EVD_OPT_SLICES changes the
+ * workspace size).  Every option has the default stated here; a value out of its
+ * range returns EVD_ERR_INVALID_ARG and leaves the plan unchanged.
+ *   EVD_OPT_SLICES        1..8  bfloat16 slices of the dense products of SBR, the
+ *                               back transformation and the D&C merges (default 8
+ *                               for EVD_FP64, 6 for EVD_SPLIT_BF16).
+ *   EVD_OPT_REFINE_ITERS  0..8  Ogita-Aishima steps after an EVD_SPLIT_BF16 solve
+ *                               (default 2; ignored for EVD_FP64).
+ *   EVD_OPT_XE_SLICES     1..8  slices of the refinement's X E product; E holds
+ *                               corrections at the error level, so few suffice
+ *                               (default 4).
+ *   EVD_OPT_BCBACK_FUSED  0, 1  allow the fused BC-Back wave kernel (default 1).
+ *   EVD_OPT_BC_KERNEL     0..2  bulge-chasing kernel: 0 band in global memory,
+ *                               1 staged in shared memory, 2 staged with the next
+ *                               step's rows carried over (default 2).
+ *   EVD_OPT_PANEL_CTAS    1..2048  CTAs of the cooperative SBR panel QR (default 64). */
+typedef enum {
+  EVD_OPT_SLICES = 0,
+  EVD_OPT_REFINE_ITERS = 1,
+  EVD_OPT_BCBACK_FUSED = 2,
+  EVD_OPT_BC_KERNEL = 3,
+  EVD_OPT_PANEL_CTAS = 4,
+  EVD_OPT_XE_SLICES = 5
+} evd_option_t;
+evd_status_t evd_plan_set_option(evd_plan_t plan, evd_option_t option, int value);
+evd_status_t evd_plan_get_option(evd_plan_t plan, evd_option_t option, int* value);
+
 /* The plan's chosen band width and double-blocking width. */
 evd_status_t evd_plan_get_blocking(evd_plan_t plan, int* b, int* nb);
 
@@ -125,6 +154,18 @@ evd_status_t evd_refine(evd_plan_t plan, const double* A0, double* w, double* Q,
  * stage-specific index (e.g. the leaf or root that failed), 0 if none.  Clears the
  * status word. */
 evd_status_t evd_plan_status(evd_plan_t plan, int* info);
+
+/* Self-test of the bounded device waits (failure detection without a fault).
+ * Enqueues on the plan's stream one kernel whose wait never completes and gives up
+ * after a short limit (well under a second), through the same wait helpers the
+ * solver uses: kind 0 a progress flag that nothing publishes, kind 1 a grid
+ * barrier that expects one CTA more than the launch has, kind 2 an mbarrier that
+ * nobody arrives at, in a CTA that holds tensor memory (freed before it returns).
+ * The kernel returns; evd_plan_status() then reports EVD_ERR_TIMEOUT with info =
+ * 9901, 9902 or 9903, clears the status word and the barrier counters, and the
+ * plan stays usable.  The paper has no counterpart (the solver's waits are this
+ * design's). */
+evd_status_t evd_wait_selftest(evd_plan_t plan, int kind);
 
 /* Destroy a plan (syncs its stream first).  NULL is a no-op. */
 void evd_plan_destroy(evd_plan_t plan);

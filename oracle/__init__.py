@@ -18,6 +18,7 @@ Functions (each restates the passage cited in the C source):
 * ``metrics(...)``         the error measures of Sec. 3.3.1 / Table 2 and the
                            acceptance bounds
 * ``refine(...)``          one Ogita-Aishima eigenpair refinement step
+* ``refine_steps(...)``    several steps, the cluster threshold held
 * ``ozaki_split(...)``     reference error-free splitting of FP64 rows into
                            integer slices (definition written out)
 
@@ -184,5 +185,5 @@ def eigh(A, want_vectors=True):
 
 
 from .metrics import metrics, acceptance  # noqa: E402,F401
-from .refine import refine  # noqa: E402,F401
+from .refine import refine, refine_steps  # noqa: E402,F401
 from .ozaki import ozaki_split, ozaki_exact_products, ozaki_value  # noqa: E402,F401

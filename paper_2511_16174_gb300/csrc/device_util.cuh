@@ -27,14 +27,14 @@ __device__ inline void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Wait until *flag >= target.  Bounded: after kSpinLimit polls the status word gets
+// Wait until *flag >= target.  Bounded: after `limit` polls the status word gets
 // EVD_ERR_TIMEOUT (info = where) and the function returns false.  Also returns
 // false as soon as another CTA has raised the abort flag (status[2]).
-__device__ inline bool wait_geq(const int* flag, int target, int* st, int where) {
+__device__ inline bool wait_geq(const int* flag, int target, int* st, int where, long long limit = kSpinLimit) {
   // busy polling first (the waits on the critical path are short), then back off
   for (int it = 0; it < 20000; ++it)
     if (ld_acquire(flag) >= target) return true;
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     if (ld_acquire(flag) >= target) return true;
     if (ld_acquire(st + 2) != 0) return false;
     __nanosleep(64);
@@ -45,9 +45,11 @@ __device__ inline bool wait_geq(const int* flag, int target, int* st, int where)
 }
 
 // Grid barrier for a cooperative launch (all CTAs co-resident).  bar[0] counts
-// arrivals, bar[1] is the generation.  Bounded; returns false on timeout/abort,
-// after which every CTA must return.
-__device__ inline bool grid_barrier(unsigned* bar, unsigned nblocks, int* st, int where) {
+// arrivals, bar[1] is the generation.  Bounded (`limit` polls); returns false on
+// timeout/abort, after which every CTA must return.  A barrier that timed out
+// leaves its arrival count behind: evd_plan_status clears it with the status word.
+__device__ inline bool grid_barrier(unsigned* bar, unsigned nblocks, int* st, int where,
+                                    long long limit = kSpinLimit) {
   __syncthreads();
   __shared__ int ok_s;
   if (threadIdx.x == 0) {
@@ -63,12 +65,12 @@ __device__ inline bool grid_barrier(unsigned* bar, unsigned nblocks, int* st, in
       long long it = 0;
       bool done = false;
       for (int q = 0; q < 20000 && !done; ++q) done = (ld_acquire_u(bar + 1) != gen);
-      for (; !done && it < kSpinLimit; ++it) {
+      for (; !done && it < limit; ++it) {
         if (ld_acquire_u(bar + 1) != gen) break;
         if (ld_acquire(st + 2) != 0) { ok_s = 0; break; }
         __nanosleep(32);
       }
-      if (it == kSpinLimit) {
+      if (!done && it == limit) {
         dev_set_status(st, EVD_ERR_TIMEOUT, where);
         atomicExch(st + 2, 1);
         ok_s = 0;

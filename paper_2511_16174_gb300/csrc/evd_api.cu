@@ -118,8 +118,8 @@ WsLayout make_layout(const PlanCore& pc, void* ws) {
                         pc.prec == EVD_SPLIT_BF16 ? refine_union_bytes(n) : (size_t)0});
   L.uni = c.take<char>(ub);
   L.uni_bytes = ub;
-  size_t gb = std::max(gemm_scratch_bytes(n, n, n, pc.slices),
-                       pc.prec == EVD_SPLIT_BF16 ? gemm_scratch_bytes(n, n, n, pc.ref_slices) : (size_t)0);
+  // the D&C merges and the refinement residuals run at ref_slices in every mode
+  size_t gb = std::max(gemm_scratch_bytes(n, n, n, pc.slices), gemm_scratch_bytes(n, n, n, pc.ref_slices));
   L.gemm_ws = c.take<char>(gb);
   L.gemm_bytes = gb;
   L.total = align_up(c.off, 256);
@@ -249,9 +249,6 @@ void fill_core(PlanCore& c, int64_t n, int64_t lda, evd_job_t job, evd_prec_t pr
   c.slices = (prec == EVD_SPLIT_BF16) ? 6 : 8;
   c.ref_slices = 8;
   c.refine_iters = (prec == EVD_SPLIT_BF16) ? 2 : 0;
-  if (const char* s = getenv("EVD_SLICES")) c.slices = atoi(s);
-  if (const char* s = getenv("EVD_REFINE_ITERS")) c.refine_iters = std::max(0, atoi(s));
-  if (const char* s = getenv("EVD_PANEL_CTAS")) c.panel_ctas = std::max(1, atoi(s));
 }
 
 size_t plan_workspace_bytes(int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb) {
@@ -312,6 +309,57 @@ evd_status_t evd_plan_create(evd_plan_t* plan, int64_t n, int64_t lda, evd_job_t
   c.status = p->d_status;
   *plan = p;
   return EVD_OK;
+}
+
+evd_status_t evd_plan_set_option(evd_plan_t p, evd_option_t opt, int value) {
+  if (!p) return EVD_ERR_INVALID_ARG;
+  PlanCore& c = p->core;
+  switch (opt) {
+    case EVD_OPT_SLICES:
+      if (value < 1 || value > 8) return EVD_ERR_INVALID_ARG;
+      c.slices = value;
+      return EVD_OK;
+    case EVD_OPT_REFINE_ITERS:
+      if (value < 0 || value > 8) return EVD_ERR_INVALID_ARG;
+      c.refine_iters = value;
+      return EVD_OK;
+    case EVD_OPT_BCBACK_FUSED:
+      if (value != 0 && value != 1) return EVD_ERR_INVALID_ARG;
+      c.bcback_fused = value;
+      return EVD_OK;
+    case EVD_OPT_BC_KERNEL:
+      if (value < 0 || value > 2) return EVD_ERR_INVALID_ARG;
+      c.bc_kernel = value;
+      return EVD_OK;
+    case EVD_OPT_PANEL_CTAS:
+      if (value < 1 || value > kMaxPanelCtas) return EVD_ERR_INVALID_ARG;
+      c.panel_ctas = value;
+      return EVD_OK;
+    case EVD_OPT_XE_SLICES:
+      if (value < 1 || value > 8) return EVD_ERR_INVALID_ARG;
+      c.xe_slices = value;
+      return EVD_OK;
+  }
+  return EVD_ERR_INVALID_ARG;
+}
+
+evd_status_t evd_plan_get_option(evd_plan_t p, evd_option_t opt, int* value) {
+  if (!p || !value) return EVD_ERR_INVALID_ARG;
+  const PlanCore& c = p->core;
+  switch (opt) {
+    case EVD_OPT_SLICES: *value = c.slices; return EVD_OK;
+    case EVD_OPT_REFINE_ITERS: *value = c.refine_iters; return EVD_OK;
+    case EVD_OPT_BCBACK_FUSED: *value = c.bcback_fused; return EVD_OK;
+    case EVD_OPT_BC_KERNEL: *value = c.bc_kernel; return EVD_OK;
+    case EVD_OPT_PANEL_CTAS: *value = c.panel_ctas; return EVD_OK;
+    case EVD_OPT_XE_SLICES: *value = c.xe_slices; return EVD_OK;
+  }
+  return EVD_ERR_INVALID_ARG;
+}
+
+evd_status_t evd_wait_selftest(evd_plan_t p, int kind) {
+  if (!p || kind < 0 || kind > 2) return EVD_ERR_INVALID_ARG;
+  return wait_selftest(p->core, kind, p->d_prog, p->d_bar);
 }
 
 evd_status_t evd_plan_get_blocking(evd_plan_t p, int* b, int* nb) {
@@ -430,6 +478,8 @@ evd_status_t evd_plan_status(evd_plan_t p, int* info) {
   int h[kStatusWords] = {0};
   if (cudaMemcpy(h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return EVD_ERR_CUDA;
   cudaMemset(p->d_status, 0, sizeof(int) * kStatusWords);
+  // a grid barrier that gave up leaves its arrival count behind
+  if (h[0] != 0 || h[2] != 0) cudaMemset(p->d_bar, 0, sizeof(unsigned) * 4);
   if (info) *info = h[1];
   return static_cast<evd_status_t>(h[0]);
 }

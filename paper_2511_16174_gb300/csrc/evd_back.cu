@@ -194,8 +194,7 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
     if (st != EVD_OK) return st;
   }
   auto kc = [&](int64_t J) { return sweep_steps_b(n, b, J * g); };
-  static const bool fused_off = getenv("EVD_BCBACK_UNFUSED") != nullptr;
-  const bool fused = !fused_off && bcback_fused_supported(pc, Q, ldq);
+  const bool fused = pc.bcback_fused && bcback_fused_supported(pc, Q, ldq);
   if (fused) {
     const evd_status_t st = bcback_fixed_point(pc, Q, ldq, true);
     if (st != EVD_OK) return st;

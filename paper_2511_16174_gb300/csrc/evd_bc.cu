@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(BC_NT) k_bulge_chase_smem(const BcArgs a) {
 // Same reflectors, same arithmetic per entry as the other forms up to the order
 // of the dot-product partial sums.
 template <int BM>
-__global__ void __launch_bounds__(4 * BM) k_bulge_chase_carry(const BcArgs a) {
+__global__ void __launch_bounds__(4 * BM, (BM <= 32) ? 4 : 2) k_bulge_chase_carry(const BcArgs a) {
   constexpr int NT = 4 * BM, TPR = 4, LD = BM + 1;
   extern __shared__ double smb[];
   double* Ds = smb;                 // Ds[q * LD + p] = A(r0 + p, r0 + q), p >= q
@@ -574,10 +574,7 @@ evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, b
     const void* kern = (const void*)k_bulge_chase;
     size_t smem = 0;
     int nt = BC_NT;
-    static const int variant = [] {
-      const char* e = getenv("EVD_BC_KERNEL");  // 0: global, 1: staged, 2: carried (default)
-      return e ? atoi(e) : 2;
-    }();
+    const int variant = pc.bc_kernel;  // 0: global, 1: staged, 2: carried (default)
     if (variant >= 1 && pc.b <= 32) {
       kern = (variant == 2) ? (const void*)k_bulge_chase_carry<32> : (const void*)k_bulge_chase_smem<32>;
       smem = 3 * 32 * 33 * sizeof(double);

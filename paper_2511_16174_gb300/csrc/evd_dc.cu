@@ -315,11 +315,19 @@ __device__ void secular_root(int i, int k, const double* dl, const double* zl, d
   bool conv = false;
   for (int it = 0; it < 120; ++it) {
     double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0;
-    for (int j = 0; j < k; ++j) {
-      double del = (dl[j] - dorg) - tau;
-      double t = rho * zl[j] * zl[j] / del;
-      if (j <= i) { psi += t; dpsi += t / del; }
-      else { phi += t; dphi += t / del; }
+    // one reciprocal per pole (FP64 division is the costly operation here): the
+    // term rho z_j^2 / del and its derivative rho z_j^2 / del^2 share it
+    for (int j = 0; j <= i; ++j) {
+      const double r = 1.0 / ((dl[j] - dorg) - tau);
+      const double t = (rho * zl[j] * zl[j]) * r;
+      psi += t;
+      dpsi = fma(t, r, dpsi);
+    }
+    for (int j = i + 1; j < k; ++j) {
+      const double r = 1.0 / ((dl[j] - dorg) - tau);
+      const double t = (rho * zl[j] * zl[j]) * r;
+      phi += t;
+      dphi = fma(t, r, dphi);
     }
     const double g = 1.0 + psi + phi;
     const double erretm = 1.0 + fabs(psi) + fabs(phi);
@@ -391,12 +399,26 @@ __global__ void k_dc_lowner(const MergeDesc* md, const int* kk, const double* dl
   const int64_t off = M.off;
   const double rho = rho_in[blockIdx.y];
   const double dj = dl[off + j];
-  double w = ((dl[off + org[off + j]] - dj) + tau[off + j]) / rho;
+  // the products of the numerators and of the denominators are kept apart, each
+  // rescaled to [0.5, 1) every 8 factors with its binary exponent counted, so the
+  // k - 1 factors cost multiplications and one division at the end
+  double num = ((dl[off + org[off + j]] - dj) + tau[off + j]) / rho, den = 1.0;
+  int enum_ = 0, eden = 0;
+  int cnt = 0;
   for (int i = 0; i < k; ++i) {
     if (i == j) continue;
-    double lam_m_dj = (dl[off + org[off + i]] - dj) + tau[off + i];
-    w *= lam_m_dj / (dl[off + i] - dj);
+    num *= (dl[off + org[off + i]] - dj) + tau[off + i];
+    den *= dl[off + i] - dj;
+    if (++cnt == 8) {
+      int e1, e2;
+      num = frexp(num, &e1);
+      den = frexp(den, &e2);
+      enum_ += e1;
+      eden += e2;
+      cnt = 0;
+    }
   }
+  const double w = ldexp(num / den, enum_ - eden);
   zh[off + j] = copysign(sqrt(fabs(w)), zl[off + j]);
 }
 
@@ -613,7 +635,10 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
           g.B = w.Umat + (off + j0) + off * n; g.ldb = n;
           g.C = Q + (off + r0) + off * ldq; g.ldc = ldq;
           g.alpha = 1.0; g.beta = 0.0;
-          evd_status_t st = gemm(g, pc.slices, w.gemm_ws, w.gemm_ws_bytes, s);
+          // FP64-accurate in every mode: the next merge's z is the last row of Q1 and the
+          // first of Q2, and a product error at the slice level would blur the tiny
+          // entries that deflate
+          evd_status_t st = gemm(g, pc.ref_slices, w.gemm_ws, w.gemm_ws_bytes, s);
           if (st != EVD_OK) return st;
         }
       }

@@ -95,7 +95,10 @@ struct PlanCore {
   cudaStream_t stream = nullptr;
   int device = 0;
   int sms = 0;
-  int panel_ctas = 64;    // CTAs of the cooperative panel QR (EVD_PANEL_CTAS overrides)
+  int panel_ctas = 64;    // CTAs of the cooperative panel QR
+  int bcback_fused = 1;   // allow the fused BC-Back wave kernel
+  int bc_kernel = 2;      // bulge chasing: 0 global memory, 1 shared-memory staged, 2 carried
+  int xe_slices = 4;      // slices of the refinement's X E product (E is at the error level)
   int* status = nullptr;  // device int[kStatusWords]
 };
 
@@ -189,6 +192,10 @@ struct RefineWork {
 };
 evd_status_t refine_run(const PlanCore& pc, const double* A0, int64_t lda0, double* w, double* Q,
                         int64_t ldq, int iters, const RefineWork& rw);
+
+// Self-test of the bounded waits (evd_selftest.cu): kind 0 progress flag, 1 grid
+// barrier, 2 mbarrier in a CTA holding tensor memory.
+evd_status_t wait_selftest(const PlanCore& pc, int kind, int* flag_zero, unsigned* bar);
 
 // ---------------------------------------------------------------- stats (evd_stats.cu)
 // RAII scope: when stats are enabled, records CUDA events around the enclosed

@@ -80,9 +80,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; raises *abort (shared) and the status word on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort, int* st, int where) {
-  for (long long i = 0; i < OZ_WAIT_LIMIT; ++i) {
+// Bounded wait (`limit` polls); raises *abort (shared) and the status word on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort, int* st, int where,
+                                          long long limit = OZ_WAIT_LIMIT) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(a, parity)) return true;
     if (*abort) return false;
   }

@@ -28,6 +28,7 @@ _sz = ctypes.c_size_t
 
 EVD_VALUES, EVD_VECTORS = 0, 1
 EVD_FP64, EVD_SPLIT_INT8, EVD_SPLIT_BF16 = 0, 1, 2
+OPTIONS = {"slices": 0, "refine_iters": 1, "bcback_fused": 2, "bc_kernel": 3, "panel_ctas": 4, "xe_slices": 5}
 STATUS = ["EVD_OK", "EVD_ERR_INVALID_ARG", "EVD_ERR_WORKSPACE", "EVD_ERR_OOM", "EVD_ERR_CUDA",
           "EVD_ERR_NONFINITE", "EVD_ERR_NO_CONVERGENCE", "EVD_ERR_TIMEOUT", "EVD_ERR_NOT_SUPPORTED"]
 
@@ -35,6 +36,8 @@ _SIGS = {
     "evd_plan_create": ([ctypes.POINTER(_vp), _i64, _i64, _int, _int, _int, _int, _vp], _int),
     "evd_plan_workspace_size": ([_vp, ctypes.POINTER(_sz)], _int),
     "evd_plan_get_blocking": ([_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)], _int),
+    "evd_plan_set_option": ([_vp, _int, _int], _int),
+    "evd_plan_get_option": ([_vp, _int, ctypes.POINTER(_int)], _int),
     "evd_sbr": ([_vp, _vp, _vp], _int),
     "evd_bulge_chase": ([_vp, _vp, _vp, _vp], _int),
     "evd_tridiag_solve": ([_vp, _vp, _vp, _vp, _i64, _vp], _int),
@@ -42,6 +45,7 @@ _SIGS = {
     "evd_syevd": ([_vp, _vp, _vp, _vp, _i64, _vp], _int),
     "evd_refine": ([_vp, _vp, _vp, _vp, _i64, _int, _vp], _int),
     "evd_plan_status": ([_vp, ctypes.POINTER(_int)], _int),
+    "evd_wait_selftest": ([_vp, _int], _int),
     "evd_plan_destroy": ([_vp], None),
     "evd_status_string": ([_int], ctypes.c_char_p),
     "evd_batched_workspace_size": ([_int, ctypes.POINTER(_i64), _int, ctypes.POINTER(_sz)], _int),
@@ -117,7 +121,7 @@ class Plan:
     """Mirror of evd_plan_t.  job: 'N' (values) or 'V' (vectors); prec: 'fp64' or
     'split_bf16' ('split_int8' is rejected with EVD_ERR_NOT_SUPPORTED)."""
 
-    def __init__(self, n, lda=None, job="V", prec="fp64", b=0, nb=0, stream=None):
+    def __init__(self, n, lda=None, job="V", prec="fp64", b=0, nb=0, stream=None, options=None):
         self.n = int(n)
         self.lda = int(lda if lda is not None else max(1, n))
         self.job = EVD_VECTORS if job in ("V", EVD_VECTORS, True) else EVD_VALUES
@@ -127,12 +131,19 @@ class Plan:
         _check(_lib.evd_plan_create(ctypes.byref(h), self.n, self.lda, self.job, self.prec, int(b), int(nb),
                                     _stream_ptr(stream)), "evd_plan_create")
         self._h = h
+        for key, value in (options or {}).items():
+            _check(_lib.evd_plan_set_option(h, OPTIONS[key], int(value)), f"evd_plan_set_option({key})")
         bb, nbb = _int(), _int()
         _lib.evd_plan_get_blocking(h, ctypes.byref(bb), ctypes.byref(nbb))
         self.b, self.nb = bb.value, nbb.value
         sz = _sz()
         _check(_lib.evd_plan_workspace_size(h, ctypes.byref(sz)), "evd_plan_workspace_size")
         self.workspace_bytes = sz.value
+
+    def option(self, key):
+        v = _int()
+        _check(_lib.evd_plan_get_option(self._h, OPTIONS[key], ctypes.byref(v)), "evd_plan_get_option")
+        return v.value
 
     def workspace(self, device="cuda"):
         return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
@@ -170,6 +181,9 @@ class Plan:
         _check(_lib.evd_refine(self._h, _ptr(A0), _ptr(w), _ptr(Q), _ld(Q), int(iterations), _ptr(ws)),
                "evd_refine")
 
+    def wait_selftest(self, kind):
+        _check(_lib.evd_wait_selftest(self._h, int(kind)), "evd_wait_selftest")
+
     def status(self):
         info = _int()
         code = _lib.evd_plan_status(self._h, ctypes.byref(info))
@@ -181,14 +195,14 @@ class Plan:
             raise EvdError(code, f"{where} (info {info})")
 
 
-def syevd(A, job="V", prec="fp64", b=0, nb=0, stream=None, overwrite=False):
+def syevd(A, job="V", prec="fp64", b=0, nb=0, stream=None, overwrite=False, options=None):
     """Eigen-decomposition of the symmetric float64 CUDA matrix A (lower triangle
     read).  Returns (w ascending, Q column-major) or (w, None) for job='N'."""
     n = A.shape[0]
     Awork = as_colmajor(A) if overwrite else as_colmajor(A).clone(memory_format=torch.preserve_format)
     if Awork.stride(0) != 1:
         Awork = as_colmajor(Awork)
-    plan = Plan(n, lda=_ld(Awork), job=job, prec=prec, b=b, nb=nb, stream=stream)
+    plan = Plan(n, lda=_ld(Awork), job=job, prec=prec, b=b, nb=nb, stream=stream, options=options)
     ws = plan.workspace(A.device)
     w = torch.empty(n, dtype=torch.float64, device=A.device)
     Q = empty_colmajor(n, n, device=A.device) if plan.job == EVD_VECTORS else None

@@ -305,6 +305,47 @@ def test_refine_clustered_falls_back_to_half_r():
     assert np.max(np.abs(A @ X1 - X1 * lam1)) < 1e-10
 
 
+def _mixed_pair_case():
+    """A spectrum with one pair of gap 1e-9, the eigenvectors of that pair rotated by
+    1e-4 within the pair (a coupling s_ij of 1e-13, the size a perturbation of A at
+    that level leaves), plus a 1e-8 perturbation everywhere: the first step's
+    delta (about 1e-5) holds the pair as a cluster, the second step's would not."""
+    n = 120
+    lam = np.linspace(-1.0, 1.0, n)
+    lam[61] = lam[60] + 1e-9
+    Qr, _ = np.linalg.qr(inputs.rng(33).standard_normal((n, n)))
+    A = (Qr * lam) @ Qr.T
+    A = 0.5 * (A + A.T)
+    th = 1e-4
+    X = Qr.copy()
+    X[:, 60] = np.cos(th) * Qr[:, 60] + np.sin(th) * Qr[:, 61]
+    X[:, 61] = -np.sin(th) * Qr[:, 60] + np.cos(th) * Qr[:, 61]
+    X = X + 1e-8 * inputs.rng(34).standard_normal((n, n))
+    return A, lam, X
+
+
+def test_refine_held_delta_keeps_orthogonality():
+    """Two steps with delta held: the mixed pair stays a cluster, orthogonality
+    reaches rounding level and the residual its FP64 level."""
+    A, lam, X = _mixed_pair_case()
+    n = A.shape[0]
+    lam2, X2, deltas = oracle.refine_steps(A, X, 2)
+    assert deltas[0] > 1e-9 and deltas[1] == deltas[0]
+    assert np.max(np.abs(X2.T @ X2 - np.eye(n))) < 1e-13
+    assert np.linalg.norm(A @ X2 - X2 * lam2) / (n * np.linalg.norm(A)) < 1e-14
+
+
+def test_refine_shrinking_delta_breaks_orthogonality():
+    """Failing control: the same two steps with delta recomputed afresh rotate the
+    pair by about 1e-4 in the second step and lose orthogonality to about 1e-8."""
+    A, lam, X = _mixed_pair_case()
+    n = A.shape[0]
+    _, X1, info1 = oracle.refine(A, X)
+    _, X2, info2 = oracle.refine(A, X1)
+    assert info2["delta"] < 1e-9 < info1["delta"]
+    assert np.max(np.abs(X2.T @ X2 - np.eye(n))) > 1e-10
+
+
 # ---------------------------------------------------------------- error-free splitting
 def test_ozaki_split_exact_rational_definition():
     r = inputs.rng(40)

@@ -216,7 +216,11 @@ def ours(args):
     del A0
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
-    options = {"refine_iters": args.refine_iters} if args.refine_iters is not None else None
+    options = {}
+    if args.refine_iters is not None:
+        options["refine_iters"] = args.refine_iters
+    if args.order is not None:
+        options["order"] = args.order
     plan = evd.Plan(n, job="V", prec=args.prec, b=args.b, nb=args.nb, stream=stream, options=options)
     ws = plan.workspace()
     Aw = evd.empty_colmajor(n, n)
@@ -358,6 +362,7 @@ def ours(args):
                        "b": plan.b, "nb": plan.nb, "seconds_per_solve": ms / 1e3,
                        "paper_tflops_4n3": 4.0 * n ** 3 / (ms / 1e3) / 1e12,
                        "refine_iters": plan.option("refine_iters") if args.prec != "fp64" else 0,
+                       "order": "reordered (Sec. 3.3)" if plan.option("order") == 1 else "conventional",
                        "l2": "inputs larger than L2 (A is 8 n^2 bytes)", "parallelism": f"replicas{ws_}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "accuracy": acc, "stages": breakdown,
@@ -404,6 +409,8 @@ def main():
     ap.add_argument("--b", type=int, default=0)
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--refine-iters", type=int, default=None, help="refinement steps of the split form")
+    ap.add_argument("--order", type=int, default=None, choices=[0, 1],
+                    help="back transformation: 0 conventional, 1 reordered (default: the library's choice)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="no per-category event timing in the timed region")
     ap.add_argument("--profile", choices=["gemm", "solve"], default=None,

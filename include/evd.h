@@ -95,14 +95,26 @@ evd_status_t evd_plan_workspace_size(evd_plan_t plan, size_t* bytes);
  *   EVD_OPT_BC_KERNEL     0..2  bulge-chasing kernel: 0 band in global memory,
  *                               1 staged in shared memory, 2 staged with the next
  *                               step's rows carried over (default 2).
- *   EVD_OPT_PANEL_CTAS    1..2048  CTAs of the cooperative SBR panel QR (default 64). */
+ *   EVD_OPT_PANEL_CTAS    1..2048  CTAs of the cooperative SBR panel QR (default 64).
+ *   EVD_OPT_BC_CTAS_PER_SM 0..4  bulge-chasing sweeps in flight per SM (at most
+ *                               what fits; default 0 = two when more sweeps can run
+ *                               at once than 2.5 x the SM count, else one).
+ *   EVD_OPT_ORDER         -1..1 order of the back transformation in evd_syevd:
+ *                               0 conventional (Sec. 2.1.2: X = Q_d, BC-Back, SBR-Back);
+ *                               1 reordered (Sec. 3.3: Q_sb = Q_s Q_b I while D&C runs
+ *                               on a second stream, then Q = Q_sb Q_d; needs b = 64,
+ *                               n >= 1024, the fused BC-Back and n^2 more doubles of
+ *                               workspace); -1 (default) reordered from n = 8192 up.
+ *                               evd_plan_get_option reports the order a solve takes. */
 typedef enum {
   EVD_OPT_SLICES = 0,
   EVD_OPT_REFINE_ITERS = 1,
   EVD_OPT_BCBACK_FUSED = 2,
   EVD_OPT_BC_KERNEL = 3,
   EVD_OPT_PANEL_CTAS = 4,
-  EVD_OPT_XE_SLICES = 5
+  EVD_OPT_XE_SLICES = 5,
+  EVD_OPT_BC_CTAS_PER_SM = 6,
+  EVD_OPT_ORDER = 7
 } evd_option_t;
 evd_status_t evd_plan_set_option(evd_plan_t plan, evd_option_t option, int value);
 evd_status_t evd_plan_get_option(evd_plan_t plan, evd_option_t option, int* value);

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "evd_internal.h"
@@ -26,6 +27,13 @@ struct WsLayout {
   double* A0 = nullptr;     // split mode: copy of A for the refinement residuals
   double* Qd_int = nullptr; // values-only: D&C still forms Q_d here
   double* e = nullptr;      // sub-diagonal of T between BC and D&C
+  // reordered stages only: Q_s Q_b (ld ldx), the scratch of the BC-Back waves while
+  // D&C holds the union region and the product scratch, and the column-range table
+  double* Xsb = nullptr;
+  int64_t ldx = 0;
+  char* bb_scratch = nullptr;
+  size_t bb_bytes = 0;
+  int2* ranges = nullptr;
   // union region
   char* uni = nullptr;
   size_t uni_bytes = 0;
@@ -40,6 +48,10 @@ struct evd_plan_s {
   unsigned* d_bar = nullptr; // 2 words
   int* d_prog = nullptr;     // n ints
   bool own_stream = false;
+  // reordered stages: BC-Back of the identity on a high-priority stream and D&C on a
+  // low-priority one, forked from and joined back to the plan's stream with events
+  cudaStream_t hi = nullptr, lo = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join_hi = nullptr, ev_join_lo = nullptr;
 };
 
 namespace {
@@ -114,6 +126,13 @@ WsLayout make_layout(const PlanCore& pc, void* ws) {
     L.Qd_int = c.take<double>((size_t)n * n);
   }
   if (pc.prec == EVD_SPLIT_BF16) L.A0 = c.take<double>((size_t)n * n);
+  if (reordered_stages(pc)) {
+    L.ldx = n + (n & 1);  // even: the fused waves' tensor copies want a 16-byte column stride
+    L.Xsb = c.take<double>((size_t)L.ldx * n);
+    L.bb_bytes = bcback_fused_scratch_bytes(n, b, pc.ref_slices);
+    L.bb_scratch = c.take<char>(L.bb_bytes);
+    L.ranges = c.take<int2>((size_t)std::max<int64_t>(bc_num_groups(n, b), 1));
+  }
   size_t ub = std::max({sbr_union_bytes(n, b, pc.nb), dc_union_bytes(n), back_union_bytes(n, b),
                         pc.prec == EVD_SPLIT_BF16 ? refine_union_bytes(n) : (size_t)0});
   L.uni = c.take<char>(ub);
@@ -222,6 +241,17 @@ int default_b(int64_t n) { return n >= 4096 ? 64 : 32; }
 }  // namespace
 
 namespace evd {
+
+// Reordered stages (Sec. 3.3): the back transformation is applied to the identity,
+// Q_sb = Q_s Q_b, while D&C computes Q_d on a side stream, and Q = Q_sb Q_d is one
+// more product.  It needs the fused BC-Back waves (b = 64, 6 or 8 slices).
+bool reordered_stages(const PlanCore& c) {
+  const bool eligible = c.job == EVD_VECTORS && c.b == 64 && (c.slices == 6 || c.slices == 8) && c.n >= 1024 &&
+                        c.n < ((int64_t)1 << 31) && c.bcback_fused;
+  if (c.order == 0) return false;
+  if (c.order == 1) return eligible;
+  return eligible && c.n >= kReorderMinN;
+}
 
 // The plan's tunables.  b = nb = 0: the autotuner's cached choice (file named by
 // EVD_AUTOTUNE_CACHE) if there is one, else b = 64 for n >= 4096 and 32 below,
@@ -339,6 +369,14 @@ evd_status_t evd_plan_set_option(evd_plan_t p, evd_option_t opt, int value) {
       if (value < 1 || value > 8) return EVD_ERR_INVALID_ARG;
       c.xe_slices = value;
       return EVD_OK;
+    case EVD_OPT_BC_CTAS_PER_SM:
+      if (value < 0 || value > 4) return EVD_ERR_INVALID_ARG;
+      c.bc_ctas_per_sm = value;
+      return EVD_OK;
+    case EVD_OPT_ORDER:
+      if (value < -1 || value > 1) return EVD_ERR_INVALID_ARG;
+      c.order = value;
+      return EVD_OK;
   }
   return EVD_ERR_INVALID_ARG;
 }
@@ -353,6 +391,8 @@ evd_status_t evd_plan_get_option(evd_plan_t p, evd_option_t opt, int* value) {
     case EVD_OPT_BC_KERNEL: *value = c.bc_kernel; return EVD_OK;
     case EVD_OPT_PANEL_CTAS: *value = c.panel_ctas; return EVD_OK;
     case EVD_OPT_XE_SLICES: *value = c.xe_slices; return EVD_OK;
+    case EVD_OPT_BC_CTAS_PER_SM: *value = c.bc_ctas_per_sm; return EVD_OK;
+    case EVD_OPT_ORDER: *value = reordered_stages(c) ? 1 : 0; return EVD_OK;
   }
   return EVD_ERR_INVALID_ARG;
 }
@@ -440,6 +480,75 @@ evd_status_t evd_refine(evd_plan_t p, const double* A0, double* w, double* Q, in
   return refine_run(p->core, A0, p->core.lda, w, Q, ldq, iterations, refine_work(p, L));
 }
 
+namespace {
+
+evd_status_t ensure_side_streams(evd_plan_t p) {
+  if (p->hi) return EVD_OK;
+  int least = 0, greatest = 0;
+  EVD_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  EVD_CUDA_TRY(cudaStreamCreateWithPriority(&p->hi, cudaStreamNonBlocking, greatest));
+  EVD_CUDA_TRY(cudaStreamCreateWithPriority(&p->lo, cudaStreamNonBlocking, least));
+  EVD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  EVD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join_hi, cudaEventDisableTiming));
+  EVD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join_lo, cudaEventDisableTiming));
+  return EVD_OK;
+}
+
+// Stages 3 and 4 in the reordered order (Sec. 3.3).  On entry (d, e) = (w, etmp) hold
+// T and ws the BC and SBR reflectors.  D&C runs on the plan's low-priority stream,
+// issued from a host thread of its own (its merges read deflation counts on the
+// host), and writes Q_d into Q.  Meanwhile the high-priority stream computes
+// X = Q_b I in ws (the fused waves skip the column tiles that are still zero): its
+// CTAs are dispatched first, and D&C's small FP64 kernels run in the room a wave CTA
+// leaves on its SM.  Once both are done (D&C holds the union region and the product
+// scratch), the plan's stream applies X <- Q_s X and forms Q = X Q_d.
+evd_status_t reordered_back(evd_plan_t p, const WsLayout& L, const double* A, double* w, double* etmp, double* Q,
+                            int64_t ldq) {
+  const PlanCore& pc = p->core;
+  cudaStream_t s0 = pc.stream;
+  evd_status_t st = ensure_side_streams(p);
+  if (st != EVD_OK) return st;
+  EVD_CUDA_TRY(cudaEventRecord(p->ev_fork, s0));
+  EVD_CUDA_TRY(cudaStreamWaitEvent(p->hi, p->ev_fork, 0));
+  EVD_CUDA_TRY(cudaStreamWaitEvent(p->lo, p->ev_fork, 0));
+  PlanCore cs = pc;
+  cs.stream = p->lo;
+  PlanCore ch = pc;
+  ch.stream = p->hi;
+  const DcWork dw = dc_work(p, L);
+  evd_status_t st_dc = EVD_OK;
+  std::thread dc_thread([&] {
+    if (cudaSetDevice(pc.device) != cudaSuccess) {
+      st_dc = EVD_ERR_CUDA;
+      return;
+    }
+    st_dc = dc_run(cs, w, etmp, Q, ldq, dw);
+  });
+  BackWork bw;
+  bw.gemm_ws = L.bb_scratch;
+  bw.gemm_ws_bytes = L.bb_bytes;
+  st = bc_back_run(ch, bc_work(p, L), L.Xsb, L.ldx, bw, L.ranges);
+  dc_thread.join();
+  // join whatever both streams queued, even after an error, so that the order holds
+  cudaEventRecord(p->ev_join_hi, p->hi);
+  cudaEventRecord(p->ev_join_lo, p->lo);
+  cudaStreamWaitEvent(s0, p->ev_join_hi, 0);
+  cudaStreamWaitEvent(s0, p->ev_join_lo, 0);
+  if (st != EVD_OK) return st;
+  if (st_dc != EVD_OK) return st_dc;
+  st = sbr_back_run(pc, A, L.sbr_T, L.sbr_tau, L.Xsb, L.ldx, back_work(p, L));
+  if (st != EVD_OK) return st;
+  // Q = X Q_d.  C is B: the split product reads B only while splitting it into the
+  // scratch, before the tensor-core kernel writes C (beta = 0).
+  Gemm gf;
+  gf.m = pc.n; gf.n = pc.n; gf.k = pc.n; gf.A = L.Xsb; gf.lda = L.ldx; gf.B = Q; gf.ldb = ldq;
+  gf.C = Q; gf.ldc = ldq; gf.alpha = 1.0; gf.beta = 0.0;
+  gf.force_tc = true; gf.status = pc.status; gf.tag = "final_gemm";
+  return gemm(gf, pc.slices, L.gemm_ws, L.gemm_bytes, s0);
+}
+
+}  // namespace
+
 evd_status_t evd_syevd(evd_plan_t p, double* A, double* w, double* Q, int64_t ldq, void* ws) {
   if (!p) return EVD_ERR_INVALID_ARG;
   const int64_t n = p->core.n;
@@ -459,10 +568,12 @@ evd_status_t evd_syevd(evd_plan_t p, double* A, double* w, double* Q, int64_t ld
   double* etmp = L.e;
   st = evd_bulge_chase(p, ws, w, etmp);
   if (st != EVD_OK) return st;
-  st = evd_tridiag_solve(p, w, etmp, vec ? Q : nullptr, ldq, ws);
-  if (st != EVD_OK) return st;
+  if (!(vec && reordered_stages(p->core))) {
+    st = evd_tridiag_solve(p, w, etmp, vec ? Q : nullptr, ldq, ws);
+    if (st != EVD_OK) return st;
+  }
   if (!vec) return EVD_OK;
-  st = evd_back_transform(p, A, ws, Q, ldq);
+  st = reordered_stages(p->core) ? reordered_back(p, L, A, w, etmp, Q, ldq) : evd_back_transform(p, A, ws, Q, ldq);
   if (st != EVD_OK) return st;
   if (p->core.prec == EVD_SPLIT_BF16 && p->core.refine_iters > 0)
     st = refine_run(p->core, L.A0, n, w, Q, ldq, p->core.refine_iters, refine_work(p, L));
@@ -487,6 +598,15 @@ evd_status_t evd_plan_status(evd_plan_t p, int* info) {
 void evd_plan_destroy(evd_plan_t p) {
   if (!p) return;
   cudaStreamSynchronize(p->core.stream);
+  if (p->hi) {
+    cudaStreamSynchronize(p->hi);
+    cudaStreamSynchronize(p->lo);
+    cudaStreamDestroy(p->hi);
+    cudaStreamDestroy(p->lo);
+    cudaEventDestroy(p->ev_fork);
+    cudaEventDestroy(p->ev_join_hi);
+    cudaEventDestroy(p->ev_join_lo);
+  }
   cudaFree(p->d_status);
   cudaFree(p->d_bar);
   cudaFree(p->d_prog);

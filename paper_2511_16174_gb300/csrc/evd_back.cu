@@ -24,8 +24,10 @@
 // is therefore one batched pair of products: W_p^T = X_p^T V_p and X_p -= Y_p W_p,
 // about 2n/b waves in all instead of n^2/(2 b g) separate groups.
 #include <algorithm>
+#include <climits>
 #include <cstdlib>
 #include <cstdio>
+#include <vector>
 
 #include "device_util.cuh"
 #include "evd_internal.h"
@@ -171,15 +173,29 @@ __global__ void k_explicit_v(const double* A, int64_t lda, int64_t r0, int64_t c
 
 int64_t bc_wave_max_groups(int64_t n, int b) { return (b > 0) ? n / (2 * (int64_t)b) + 2 : 1; }
 
-evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w) {
+int64_t bc_num_groups(int64_t n, int b) {
+  if (n < 3 || b < 2) return 0;
+  const int64_t nJ = ceil_div(n - 2, b);
+  int64_t total = 0;
+  for (int64_t J = 0; J < nJ; ++J) total += sweep_steps_b(n, b, J * b);
+  return total;
+}
+
+evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
+                         int2* ident_ranges) {
   const int64_t n = pc.n;
+  if (ident_ranges) {
+    // BC-Back of the identity (reordered stages): X = I first
+    const evd_status_t st = set_identity(Q, ldq, n, pc.stream);
+    if (st != EVD_OK) return st;
+  }
   if (n < 3 || pc.b < 2) return EVD_OK;
   const int b = pc.b, g = pc.b;
   const int h = g + b - 1;
   const size_t smem = ((size_t)h * g + (size_t)g * g + 2 * g) * sizeof(double);
   // small problems, and band widths whose group factors do not fit in shared
   // memory (b > 64): reflector-by-reflector kernel on FP64 cores
-  if (pc.slices <= 0 || n < 1024 || !w.Vg || smem > kMaxDynamicSmem) {
+  if (pc.slices <= 0 || n < 1024 || (!w.Vg && !ident_ranges) || smem > kMaxDynamicSmem) {
     const unsigned grid = (unsigned)ceil_div(n, BB_NC);
     StatScope sc("bc_back", pc.stream, 4.0 * pc.b * (double)n * (double)bc_num_reflectors(n, pc.b));
     k_bc_back<<<grid, BB_NT, 0, pc.stream>>>(bw.U, bw.Utau, n, pc.b, pc.b, Q, ldq); count_launch();
@@ -195,11 +211,50 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   }
   auto kc = [&](int64_t J) { return sweep_steps_b(n, b, J * g); };
   const bool fused = pc.bcback_fused && bcback_fused_supported(pc, Q, ldq);
+  if (ident_ranges && !fused) return EVD_ERR_INVALID_ARG;  // the identity start needs the fused waves
   if (fused) {
     const evd_status_t st = bcback_fixed_point(pc, Q, ldq, true);
     if (st != EVD_OK) return st;
   }
   const int64_t tmax = kc(0) + nJ - 2;
+  // Identity start: the column tiles each group's rows can be nonzero in.  X = I
+  // at first, so row r is nonzero in column r only; a group mixes its rows, so
+  // afterwards all of them are nonzero at most over the union of their column
+  // ranges.  With g = b the group G(J, k) covers rows (J+k) b + 1 .. (J+k+2) b - 1,
+  // inside the b-row blocks q = J + k and q + 1 (block q: rows q b + 1 .. q b + b),
+  // and the groups of one launch cover disjoint blocks, so tracking one column
+  // interval per block, in launch order, gives a superset of every group's support.
+  std::vector<int2> ranges;
+  std::vector<int64_t> launch_off;
+  if (ident_ranges) {
+    const int64_t nblk = n / b + 3;
+    std::vector<int64_t> cmin(nblk), cmax(nblk);
+    for (int64_t q = 0; q < nblk; ++q) {
+      cmin[q] = std::min<int64_t>(q * b + 1, n - 1);
+      cmax[q] = std::min<int64_t>(q * b + b, n - 1);
+    }
+    ranges.reserve((size_t)bc_num_groups(n, b));
+    for (int64_t t = 0; t <= tmax; ++t) {
+      int64_t jp = std::min<int64_t>(t, nJ - 1);
+      while (jp >= 0) {
+        if (t - jp >= kc(nJ - 1 - jp)) { --jp; continue; }
+        const int64_t jhi = jp;
+        while (jp >= 0 && t - jp < kc(nJ - 1 - jp)) --jp;
+        const int64_t jlo = jp + 1;
+        launch_off.push_back((int64_t)ranges.size());
+        for (int64_t jq = jlo; jq <= jhi; ++jq) {
+          const int64_t q = (nJ - 1 - jq) + (t - jq);  // J + k
+          const int64_t lo = std::min(cmin[q], cmin[q + 1]), hi = std::max(cmax[q], cmax[q + 1]);
+          cmin[q] = cmin[q + 1] = lo;
+          cmax[q] = cmax[q + 1] = hi;
+          ranges.push_back(make_int2((int)(lo / 128), (int)(hi / 128)));
+        }
+      }
+    }
+    EVD_CUDA_TRY(cudaMemcpyAsync(ident_ranges, ranges.data(), ranges.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                 s));
+  }
+  size_t launch_idx = 0;
   for (int64_t t = 0; t <= tmax; ++t) {
     // groups of wave t: J' = nJ - 1 - J in [jlo, jhi] with 0 <= k = t - J' < kc(J)
     int64_t jp = std::min<int64_t>(t, nJ - 1);
@@ -214,8 +269,21 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
       const int64_t J0f = nJ - 1 - jlo, k0f = t - jlo;
       const int64_t R0f = J0f * g + 1 + k0f * b;
       if (fused) {
+        WaveTiles wt;
+        if (ident_ranges) {
+          const int64_t off = launch_off[launch_idx++];
+          wt.ranges = ident_ranges + off;
+          wt.tile0 = INT64_MAX;
+          wt.tile1 = -1;
+          for (int p = 0; p < count; ++p) {
+            const int2 r = ranges[(size_t)off + p];
+            wt.tile0 = std::min<int64_t>(wt.tile0, r.x);
+            wt.tile1 = std::max<int64_t>(wt.tile1, r.y);
+            wt.work_tiles += r.y - r.x + 1;
+          }
+        }
         const evd_status_t st = bcback_fused_wave(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0f,
-                                                  (int)std::min<int64_t>(h, n - R0f));
+                                                  (int)std::min<int64_t>(h, n - R0f), wt);
         if (st != EVD_OK) return st;
         continue;
       }

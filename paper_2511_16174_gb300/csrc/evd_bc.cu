@@ -588,7 +588,15 @@ evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, b
       const evd_status_t st = ensure_dynamic_smem(kern, smem);
       if (st != EVD_OK) return st;
     }
+    // Sweeps that can be in flight at once: a sweep of K steps starts about lag
+    // steps after its predecessor, so about K / lag run together.  Two sweeps share
+    // an SM only when there are more of those than SMs (sharing slows each sweep,
+    // and below that the chain of sweeps sets the time).
     int maxG = max_coresident_blocks(kern, nt, smem);
+    const int64_t inflight = (sweep_steps(n, pc.b, 0) + BC_LAG_CARRY - 1) / BC_LAG_CARRY;
+    int per_sm = pc.bc_ctas_per_sm;
+    if (per_sm <= 0) per_sm = (variant == 2 && inflight > (int64_t)pc.sms * 5 / 2) ? 2 : 1;
+    if (pc.sms > 0 && maxG > pc.sms * per_sm) maxG = pc.sms * per_sm;
     int64_t G = n - 2;
     if (G > maxG) G = maxG;
     void* args[] = {&a};

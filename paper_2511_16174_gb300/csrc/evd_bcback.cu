@@ -203,6 +203,8 @@ struct WaveArgs {
   const __nv_bfloat16* Yb;
   const int* eY;
   int* st;
+  int64_t tile0;       // column tile of blockIdx.x = 0 (tiles of 128 columns)
+  const int2* ranges;  // per group: the column tiles [x, y] that can be nonzero in its rows (nullptr: all)
 };
 
 // AND of a predicate over the 512 threads of warps 2..17 (named barrier 1).
@@ -376,7 +378,14 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
   int* eWs = exw + 4 * BB_H;                                 // 128, scale of W per column of X
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = blockIdx.y;
-  const int64_t c0 = (int64_t)blockIdx.x * OZ_BM;
+  const int64_t tile = a.tile0 + blockIdx.x;
+  if (a.ranges) {
+    // X's rows of this group are zero in this column tile (BC-Back of the identity):
+    // W and the update vanish.  The whole CTA leaves before any set-up.
+    const int2 r = a.ranges[p];
+    if (tile < r.x || tile > r.y) return;
+  }
+  const int64_t c0 = tile * OZ_BM;
   const int64_t R0 = a.R0 - p * a.gstride;
   const int hp = (p == 0) ? a.h0 : a.h;
   const __nv_bfloat16* Vp = a.Vb + (size_t)p * S * BB_G * BB_H;
@@ -638,7 +647,7 @@ EncodeTiledFn encode_tiled() {
 
 template <int S>
 evd_status_t launch_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w, int64_t nJ,
-                         int64_t t, int64_t jlo, int count, int64_t R0, int hh0, cudaStream_t s) {
+                         int64_t t, int64_t jlo, int count, int64_t R0, int hh0, const WaveTiles& wt, cudaStream_t s) {
   const int64_t n = pc.n;
   const int b = pc.b;
   // workspace: blobs and scales, the FP64 factors, then the products' scratch
@@ -706,11 +715,16 @@ evd_status_t launch_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   a.X = reinterpret_cast<long long*>(Q); a.ldx = ldq; a.n = n; a.R0 = R0; a.gstride = 2 * b; a.h0 = hh0;
   a.h = 2 * b - 1;
   a.Vb = Vb; a.eV = eV; a.Yb = Yb; a.eY = eY; a.st = pc.status;
-  dim3 grid((unsigned)ceil_div(n, OZ_BM), (unsigned)count);
+  a.tile0 = wt.ranges ? wt.tile0 : 0;
+  a.ranges = wt.ranges;
+  const int64_t ntiles = wt.ranges ? wt.tile1 - wt.tile0 + 1 : ceil_div(n, OZ_BM);
+  if (ntiles <= 0) return EVD_OK;
+  dim3 grid((unsigned)ntiles, (unsigned)count);
   // executed bf16 flops of the two products (tensor work of one wave)
-  const double flops = (double)count * ceil_div(n, OZ_BM) * OZ_BM * 2.0 * (BB_G * BB_H + BB_H * BB_G) *
-                       (double)(S * (S + 1) / 2);
-  StatScope sc("bc_back_wave", s, flops, (double)count * 16.0 * BB_H * (double)n, "tc_split");
+  // executed tile work (the tiles of the range table, when there is one)
+  const double tiles = wt.ranges ? (double)wt.work_tiles : (double)count * ceil_div(n, OZ_BM);
+  const double flops = tiles * OZ_BM * 2.0 * (BB_G * BB_H + BB_H * BB_G) * (double)(S * (S + 1) / 2);
+  StatScope sc("bc_back_wave", s, flops, tiles * 16.0 * BB_H * (double)OZ_BM, "tc_split");
   k_bcback_wave<S><<<grid, BB_THREADS, smem, s>>>(a);
   count_launch();
   EVD_CUDA_TRY(cudaGetLastError());
@@ -761,9 +775,28 @@ bool bcback_fused_supported(const PlanCore& pc, const double* Q, int64_t ldq) {
 }
 
 evd_status_t bcback_fused_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
-                               int64_t nJ, int64_t t, int64_t jlo, int count, int64_t R0, int hh0) {
-  if (pc.slices == 8) return launch_wave<8>(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0, hh0, pc.stream);
-  return launch_wave<6>(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0, hh0, pc.stream);
+                               int64_t nJ, int64_t t, int64_t jlo, int count, int64_t R0, int hh0,
+                               const WaveTiles& wt) {
+  if (pc.slices == 8) return launch_wave<8>(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0, hh0, wt, pc.stream);
+  return launch_wave<6>(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0, hh0, wt, pc.stream);
+}
+
+size_t bcback_fused_scratch_bytes(int64_t n, int b, int ref_slices) {
+  const int64_t count = bc_wave_max_groups(n, b);
+  Carver cv(nullptr);
+  cv.take<__nv_bfloat16>((size_t)count * 8 * BB_G * BB_H);
+  cv.take<__nv_bfloat16>((size_t)count * 8 * BB_H * BB_G);
+  cv.take<int>((size_t)count * BB_G);
+  cv.take<int>((size_t)count * BB_H);
+  cv.take<double>((size_t)count * BB_H * BB_G);
+  cv.take<double>((size_t)count * BB_H * BB_G);
+  cv.take<double>((size_t)count * BB_G * BB_G);
+  cv.take<double>((size_t)count * BB_G * BB_G);
+  cv.take<double>((size_t)count * BB_G);
+  cv.take<char>(0);
+  const size_t prod = std::max(ozaki_scratch_bytes_batched(BB_G, BB_G, BB_H, ref_slices, (int)count),
+                               ozaki_scratch_bytes_batched(BB_H, BB_G, BB_G, ref_slices, (int)count));
+  return cv.off + prod + 256;
 }
 
 }  // namespace evd

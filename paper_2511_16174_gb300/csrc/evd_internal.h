@@ -98,7 +98,9 @@ struct PlanCore {
   int panel_ctas = 64;    // CTAs of the cooperative panel QR
   int bcback_fused = 1;   // allow the fused BC-Back wave kernel
   int bc_kernel = 2;      // bulge chasing: 0 global memory, 1 shared-memory staged, 2 carried
+  int bc_ctas_per_sm = 0; // bulge-chasing CTAs (sweeps in flight) per SM, 0 = by the sweep count
   int xe_slices = 4;      // slices of the refinement's X E product (E is at the error level)
+  int order = -1;         // back transformation: 0 conventional, 1 reordered (Sec. 3.3), -1 by size
   int* status = nullptr;  // device int[kStatusWords]
 };
 
@@ -169,14 +171,32 @@ struct BackWork {
   void* gemm_ws;
   size_t gemm_ws_bytes;
 };
+// BC-Back, X <- Q_b X.  With ident_ranges (device, bc_num_groups() entries) X is set
+// to the identity first and every fused wave skips the column tiles its groups'
+// rows are still zero in (the reordered stages: Q_b I while D&C runs).
 evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq,
-                         const BackWork& w);
+                         const BackWork& w, int2* ident_ranges = nullptr);
+int64_t bc_num_groups(int64_t n, int b);
+// Whether a plan's whole-path solve runs the reordered stages (evd_api.cu).
+bool reordered_stages(const PlanCore& c);
+constexpr int64_t kReorderMinN = 8192;  // the default (order = -1) reorders from this size up
 // Fused BC-Back wave (b = 64, 6 or 8 slices; evd_bcback.cu).
 bool bcback_fused_supported(const PlanCore& pc, const double* Q, int64_t ldq);
 // X (FP64, in place) to and from the fixed point the fused waves work in.
 evd_status_t bcback_fixed_point(const PlanCore& pc, double* Q, int64_t ldq, bool to_fixed);
+// Column tiles (128 columns) one fused wave launch covers: with a range table, the
+// grid spans tiles [tile0, tile1] and the CTAs of group p outside ranges[p] leave at
+// once (BC-Back of the identity, whose rows are zero outside a known column range).
+struct WaveTiles {
+  const int2* ranges = nullptr;  // device, one per group of the launch
+  int64_t tile0 = 0, tile1 = -1;
+  int64_t work_tiles = 0;        // sum over the groups of their range lengths
+};
 evd_status_t bcback_fused_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
-                               int64_t nJ, int64_t t, int64_t jlo, int count, int64_t R0, int hh0);
+                               int64_t nJ, int64_t t, int64_t jlo, int count, int64_t R0, int hh0,
+                               const WaveTiles& wt);
+// Scratch the fused waves' prep products need (the group factors of one wave).
+size_t bcback_fused_scratch_bytes(int64_t n, int b, int ref_slices);
 evd_status_t sbr_back_run(const PlanCore& pc, const double* A, const double* sbr_T,
                           const double* sbr_tau, double* Q, int64_t ldq, const BackWork& w);
 

@@ -28,7 +28,8 @@ _sz = ctypes.c_size_t
 
 EVD_VALUES, EVD_VECTORS = 0, 1
 EVD_FP64, EVD_SPLIT_INT8, EVD_SPLIT_BF16 = 0, 1, 2
-OPTIONS = {"slices": 0, "refine_iters": 1, "bcback_fused": 2, "bc_kernel": 3, "panel_ctas": 4, "xe_slices": 5}
+OPTIONS = {"slices": 0, "refine_iters": 1, "bcback_fused": 2, "bc_kernel": 3, "panel_ctas": 4, "xe_slices": 5,
+           "bc_ctas_per_sm": 6, "order": 7}
 STATUS = ["EVD_OK", "EVD_ERR_INVALID_ARG", "EVD_ERR_WORKSPACE", "EVD_ERR_OOM", "EVD_ERR_CUDA",
           "EVD_ERR_NONFINITE", "EVD_ERR_NO_CONVERGENCE", "EVD_ERR_TIMEOUT", "EVD_ERR_NOT_SUPPORTED"]
 

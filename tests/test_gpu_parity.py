@@ -62,7 +62,8 @@ def test_sbr_band_matches_oracle(evd, n, b, nb):
     assert err <= 1e-12 * np.linalg.norm(A), err
 
 
-@pytest.mark.parametrize("n,b", [(64, 8), (100, 16), (257, 32), (512, 32), (129, 64), (200, 3)])
+@pytest.mark.parametrize("n,b", [(64, 8), (100, 16), (257, 32), (512, 32), (129, 64), (200, 3), (1100, 64),
+                                 (900, 32)])
 def test_bulge_chase_matches_oracle(evd, n, b):
     A = inputs.goe(n, 2000 + n + b)
     B_ref, _, _ = oracle.sbr(A, b)

@@ -75,14 +75,18 @@ def test_refine_two_steps_match_oracle_and_reach_fp64_bounds(evd):
     plan.refine(dev(A, evd), w, Xd, 2, ws)
     plan.check("refine")
     Xg, wg = Xd.cpu().numpy(), w.cpu().numpy()
-    # a column's rotation against its neighbours is fixed to about u ||A|| / gap, so
-    # columns are compared elementwise where the eigenvalue gap is at least 1e-4
-    # (the rest through the metrics below)
+    # E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i): an FP64-accurate s_ij carries about
+    # u ||A|| of rounding (the GPU's and numpy's differ), so a column's rotation against
+    # a neighbour at distance gap is fixed to about u ||A|| / gap per step.  Columns
+    # whose eigenvalue is at least 1e-3 from both neighbours are compared elementwise
+    # within 20 u ||A||_2 / 1e-3 (two steps, a factor 10 of margin); all columns are
+    # held to the acceptance bounds below.
     gaps = np.diff(np.sort(lam_ref))
     gap = np.minimum(np.r_[np.inf, gaps], np.r_[gaps, np.inf])[np.argsort(np.argsort(lam_ref))]
-    sep = gap >= 1e-4
+    sep = gap >= 1e-3
     assert sep.sum() > n // 2
-    assert np.max(np.abs(Xg[:, sep] - X_ref[:, sep])) <= 1e-12
+    tol = 20 * U * np.max(np.abs(lam_ref)) / 1e-3
+    assert np.max(np.abs(Xg[:, sep] - X_ref[:, sep])) <= tol
     assert np.max(np.abs(wg - lam_ref)) <= 100 * n * U * np.max(np.abs(lam_ref))
     lam = np.sort(lam)
     m = oracle.metrics(A, wg, Xg, w_ref=lam)

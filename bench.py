@@ -374,6 +374,96 @@ def ours(args):
     return 0
 
 
+def batch_mode(args):
+    """The batched configuration: 512 symmetric matrices (G + G^T) / 2, n drawn
+    log-uniformly from 64 to 2048, eigenvalues and eigenvectors, one captured graph
+    per run, against a loop of single evd_syevd calls on the same buffers.  One JSON
+    line (matrices per second); every result is checked on the GPU against the
+    acceptance bounds, and the eigenvalues of a sample against the CPU oracle."""
+    import torch
+    from paper_2511_16174_gb300 import evd, inputs
+    torch.cuda.set_device(0)
+    count = args.batch
+    sizes = [int(x) for x in inputs.batch_sizes(count, inputs.SEED_BASE + 5)]
+    batch = evd.Batch(sizes, job="V")
+    A0 = [evd.as_colmajor(inputs.goe_device(n, inputs.SEED_BASE + 1000 + i)) for i, n in enumerate(sizes)]
+    stream = torch.cuda.current_stream()
+
+    def refill():
+        for a, t in zip(A0, batch.A):
+            t.copy_(a)
+
+    def run_batch():
+        refill()
+        batch.run(stream)
+
+    plans = [evd.Plan(n, job="V", stream=stream) for n in sizes]
+    wss = [p.workspace() for p in plans]
+
+    def run_loop():
+        refill()
+        for p, ws, a, w, q in zip(plans, wss, batch.A, batch.w, batch.Q):
+            p.syevd(a, w, q, ws)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, (time.perf_counter() - t0) / args.steps * 1e3
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_loop, wall_loop = timed(run_loop)
+    for p in plans:
+        p.check("loop solve")
+    ms_batch, wall_batch = timed(run_batch)
+    clk = clocks.stop()
+    graph = evd.batched_last_graph()
+    # accuracy of the last batched run: every matrix on the GPU, a sample against the oracle
+    U = 2.0 ** -53
+    worst = {"dlam_ratio": 0.0, "orth_ratio": 0.0, "resid_ratio": 0.0}
+    with torch.no_grad():
+        for a, w, q, n in zip(A0, batch.w, batch.Q, sizes):
+            O = q.t() @ q
+            O.diagonal().sub_(1.0)
+            orth = float(O.abs().max())
+            R = a @ q - q * w[None, :]
+            resid = float(torch.linalg.matrix_norm(R) / (n * torch.linalg.matrix_norm(a)))
+            worst["orth_ratio"] = max(worst["orth_ratio"], orth / (10 * n * U))
+            worst["resid_ratio"] = max(worst["resid_ratio"], resid / (10 * U))
+    import oracle
+    sample = list(range(0, count, max(1, count // 8)))[:8]
+    for i in sample:
+        A = A0[i].cpu().numpy()
+        w_ref, _ = oracle.eigh(A, want_vectors=False)
+        dl = float(np.max(np.abs(batch.w[i].cpu().numpy() - w_ref)))
+        worst["dlam_ratio"] = max(worst["dlam_ratio"], dl / (10 * sizes[i] * U * float(np.max(np.abs(w_ref)))))
+    flops = sum(nominal_flops(n) for n in sizes)
+    line = {
+        "metric": "batched EVD matrices per second (512 matrices, n log-uniform in [64, 2048])",
+        "value": count / (ms_batch / 1e3), "unit": "matrices/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{count} x (G+G^T)/2, n log-uniform in [64, 2048] (sum n = {sum(sizes)}), "
+                               f"eigenvalues and eigenvectors, FP64",
+                   "captured_graph": graph, "tflops_nominal": flops / (ms_batch / 1e3) / 1e12},
+        "loop_of_single_solves": {"value": count / (ms_loop / 1e3), "unit": "matrices/s", "ms_per_step": ms_loop,
+                                  "host_wall_ms": wall_loop},
+        "batched_over_loop": ms_loop / ms_batch, "host_wall_ms": wall_batch,
+        "accuracy": {**worst, "oracle_sample": len(sample), "within_bounds": all(v <= 1.0 for v in worst.values())},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def profile_target(args):
     """A small, untimed run for ncu captures (no JSON line)."""
     import torch
@@ -409,6 +499,8 @@ def main():
     ap.add_argument("--b", type=int, default=0)
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--refine-iters", type=int, default=None, help="refinement steps of the split form")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="the batched configuration with this many matrices (512) instead of the single solve")
     ap.add_argument("--order", type=int, default=None, choices=[0, 1],
                     help="back transformation: 0 conventional, 1 reordered (default: the library's choice)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -418,6 +510,8 @@ def main():
     args = ap.parse_args()
     if args.profile:
         return profile_target(args)
+    if args.batch:
+        return batch_mode(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

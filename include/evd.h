@@ -188,15 +188,21 @@ const char* evd_status_string(evd_status_t status);
 /* ---------------------------------------------------------------------------
  * Batched solve: count independent symmetric problems of uneven size, each with
  * its own A (lower read, overwritten), lda, w, Q, ldq.  Problems are assigned
- * longest first (cost ~ n^3) to up to 8 concurrent lanes; each lane is a stream and
- * a host thread of its own with its own part of ws.  The lanes start after the work
- * already queued on `stream` and `stream` waits for all of them, so the call is
- * ordered like one kernel on `stream`; it returns when every problem has been
- * solved (it synchronizes the lanes to read each problem's status).  Arrays n,
- * lda, ldq are HOST arrays of length count; A, w, Q are HOST arrays of DEVICE
- * pointers.  ws/ws_bytes: device workspace of at least
+ * longest first (cost ~ n^3) to up to 8 lanes, each with its own part of ws.  The
+ * whole batch runs as one CUDA graph: every solve (a plan each, D&C in its form
+ * without host reads) is captured on its lane's stream, the lanes forked from and
+ * joined to one stream, and the graph launched once.  The captured graph and its
+ * plans are kept until the next call with different arguments: a call with exactly
+ * the same arguments launches it again without capturing.  If the driver refuses
+ * the capture, the same work runs on live lanes (a stream and host thread each);
+ * evd_batched_last_graph() reports which path the last call took.  The work starts
+ * after what is already queued on `stream`, `stream` waits for it, and the call
+ * returns once every problem has been solved (it reads each problem's status).
+ * Arrays n, lda, ldq are HOST arrays of length count; A, w, Q are HOST arrays of
+ * DEVICE pointers.  ws/ws_bytes: device workspace of at least
  * evd_batched_workspace_size() bytes (256-byte aligned).  Returns the first error
- * any problem reported.
+ * any problem reported.  Not thread-safe against concurrent batched calls on the
+ * same graph cache (calls serialize on a lock).
  * ------------------------------------------------------------------------- */
 evd_status_t evd_batched_workspace_size(int count, const int64_t* n_host, evd_job_t job,
                                         size_t* bytes);
@@ -204,6 +210,8 @@ evd_status_t evd_syevd_batched(int count, const int64_t* n_host, double* const* 
                                const int64_t* lda_host, double* const* w_host,
                                double* const* Q_host, const int64_t* ldq_host, evd_job_t job,
                                void* ws, size_t ws_bytes, void* stream);
+/* 1 if the last evd_syevd_batched call ran as a captured graph, 0 if on live lanes. */
+int evd_batched_last_graph(void);
 
 /* ---------------------------------------------------------------------------
  * The dense product engine on its own (for tests and benchmarks):
@@ -240,14 +248,17 @@ evd_status_t evd_dgemm_static(char transa, char transb, int64_t m, int64_t n, in
                               int64_t ldb, double beta, double* C, int64_t ldc, int slices,
                               void* stream);
 
-/* Autotuner: time one solve of a seeded symmetric n x n matrix (after one untimed
- * solve) for each candidate (b, nb) in {32, 64, 128}^2 with nb a multiple of b,
- * and return the fastest in *b, *nb.  With cache_path != NULL the choice is kept
- * per (n rounded to a power of two, job, prec) in that JSON file, and a cached
- * entry is returned without timing.  evd_plan_create with b = nb = 0 uses the
- * entry of the file named by the environment variable EVD_AUTOTUNE_CACHE, if
- * there is one.  Allocates its own device memory (cudaMalloc) and runs on the
- * legacy default stream; n <= 65535. */
+/* Autotuner: time one solve of a seeded symmetric n x n matrix for each candidate
+ * (b, nb) with b in {32, 64, 128} and nb in {b, 2b, 4b, 8b, 16b} below n (from
+ * n = 32768 on, b = 64 only: the fused BC-Back waves need it), then, for the
+ * fastest pair, the bulge chasing with one and with two sweeps in flight per SM
+ * (the sweep grouping); the first solve of the call is an untimed warm-up.  Returns
+ * the fastest (b, nb) in *b, *nb.  With cache_path != NULL the choice, the sweep
+ * grouping included, is kept per (n rounded to a power of two, job, prec) in that
+ * JSON file, and a cached entry is returned without timing.  evd_plan_create with
+ * b = nb = 0 uses the entry of the file named by the environment variable
+ * EVD_AUTOTUNE_CACHE, if there is one.  Allocates its own device memory
+ * (cudaMalloc) and runs on the legacy default stream; n <= 65535. */
 evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char* cache_path,
                           int* b, int* nb);
 

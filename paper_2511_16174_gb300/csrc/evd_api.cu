@@ -47,6 +47,7 @@ struct evd_plan_s {
   int* d_status = nullptr;   // kStatusWords ints
   unsigned* d_bar = nullptr; // 2 words
   int* d_prog = nullptr;     // n ints
+  void* d_tree = nullptr;    // the D&C merge tree (uploaded once)
   bool own_stream = false;
   // reordered stages: BC-Back of the identity on a high-priority stream and D&C on a
   // low-priority one, forked from and joined back to the plan's stream with events
@@ -261,10 +262,11 @@ void fill_core(PlanCore& c, int64_t n, int64_t lda, evd_job_t job, evd_prec_t pr
   c.lda = lda;
   c.job = job;
   c.prec = prec;
-  int tb = 0, tnb = 0;
-  if (b == 0 && nb == 0 && autotune_lookup(n, job, prec, &tb, &tnb)) {
+  int tb = 0, tnb = 0, tper = 0;
+  if (b == 0 && nb == 0 && autotune_lookup(n, job, prec, &tb, &tnb, &tper)) {
     c.b = tb;
     c.nb = tnb;
+    c.bc_ctas_per_sm = tper;
   } else {
     c.b = (b > 0) ? b : default_b(n);
     if (c.b < 2 && b == 0) c.b = 2;
@@ -324,16 +326,24 @@ evd_status_t evd_plan_create(evd_plan_t* plan, int64_t n, int64_t lda, evd_job_t
   c.stream = static_cast<cudaStream_t>(stream);
   cudaGetDevice(&c.device);
   cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device);
+  const size_t tree_bytes = dc_tree_bytes(n);
   if (cudaMalloc(&p->d_status, sizeof(int) * kStatusWords) != cudaSuccess ||
       cudaMalloc(&p->d_bar, sizeof(unsigned) * 4) != cudaSuccess ||
-      cudaMalloc(&p->d_prog, sizeof(int) * std::max<int64_t>(n, 1)) != cudaSuccess) {
+      cudaMalloc(&p->d_prog, sizeof(int) * std::max<int64_t>(n, 1)) != cudaSuccess ||
+      cudaMalloc(&p->d_tree, tree_bytes) != cudaSuccess) {
     cudaFree(p->d_status);
     cudaFree(p->d_bar);
     cudaFree(p->d_prog);
+    cudaFree(p->d_tree);
     (void)cudaGetLastError();
     delete p;
     return EVD_ERR_OOM;
   }
+  if (dc_tree_upload(n, p->d_tree, tree_bytes) != EVD_OK) {
+    evd_plan_destroy(p);
+    return EVD_ERR_CUDA;
+  }
+  c.dc_tree = p->d_tree;
   cudaMemset(p->d_status, 0, sizeof(int) * kStatusWords);
   cudaMemset(p->d_bar, 0, sizeof(unsigned) * 4);
   c.status = p->d_status;
@@ -396,6 +406,16 @@ evd_status_t evd_plan_get_option(evd_plan_t p, evd_option_t opt, int* value) {
   }
   return EVD_ERR_INVALID_ARG;
 }
+
+}  // extern "C"
+
+namespace evd {
+void plan_set_sync_free(evd_plan_t p, bool on) {
+  if (p) p->core.dc_sync_free = on;
+}
+}  // namespace evd
+
+extern "C" {
 
 evd_status_t evd_wait_selftest(evd_plan_t p, int kind) {
   if (!p || kind < 0 || kind > 2) return EVD_ERR_INVALID_ARG;
@@ -610,6 +630,7 @@ void evd_plan_destroy(evd_plan_t p) {
   cudaFree(p->d_status);
   cudaFree(p->d_bar);
   cudaFree(p->d_prog);
+  cudaFree(p->d_tree);
   delete p;
 }
 

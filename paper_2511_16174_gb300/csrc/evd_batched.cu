@@ -13,6 +13,7 @@
 // requested order and keeps the fastest per (n bucket, job, precision) in a JSON
 // cache file of one entry per line.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -97,6 +98,7 @@ struct CacheEntry {
   int64_t bucket;
   int job, prec, b, nb;
   double ms;
+  int bc_per_sm = 0;  // bulge-chasing sweeps in flight per SM (0: the plan's rule)
 };
 
 std::mutex g_cache_mu;
@@ -112,6 +114,8 @@ std::vector<CacheEntry> read_cache(const char* path) {
     if (sscanf(line.c_str(), " {\"n_bucket\": %lld, \"job\": %d, \"prec\": %d, \"b\": %d, \"nb\": %d, \"ms\": %lf",
                &bk, &e.job, &e.prec, &e.b, &e.nb, &e.ms) == 6) {
       e.bucket = bk;
+      const size_t at = line.find("\"bc_per_sm\": ");
+      if (at != std::string::npos) e.bc_per_sm = atoi(line.c_str() + at + 13);
       v.push_back(e);
     }
   }
@@ -124,8 +128,10 @@ void write_cache(const char* path, const std::vector<CacheEntry>& v) {
   f << "[\n";
   for (size_t i = 0; i < v.size(); ++i) {
     char buf[256];
-    snprintf(buf, sizeof(buf), "{\"n_bucket\": %lld, \"job\": %d, \"prec\": %d, \"b\": %d, \"nb\": %d, \"ms\": %.3f}%s\n",
-             (long long)v[i].bucket, v[i].job, v[i].prec, v[i].b, v[i].nb, v[i].ms, i + 1 < v.size() ? "," : "");
+    snprintf(buf, sizeof(buf),
+             "{\"n_bucket\": %lld, \"job\": %d, \"prec\": %d, \"b\": %d, \"nb\": %d, \"ms\": %.3f, \"bc_per_sm\": %d}%s\n",
+             (long long)v[i].bucket, v[i].job, v[i].prec, v[i].b, v[i].nb, v[i].ms, v[i].bc_per_sm,
+             i + 1 < v.size() ? "," : "");
     f << buf;
   }
   f << "]\n";
@@ -135,7 +141,7 @@ void write_cache(const char* path, const std::vector<CacheEntry>& v) {
 
 // Cached choice for plan creation with b = nb = 0 (no timing): the entry of the
 // file named by EVD_AUTOTUNE_CACHE for n's bucket, job and precision, if any.
-bool autotune_lookup(int64_t n, evd_job_t job, evd_prec_t prec, int* b, int* nb) {
+bool autotune_lookup(int64_t n, evd_job_t job, evd_prec_t prec, int* b, int* nb, int* bc_per_sm) {
   const char* path = getenv("EVD_AUTOTUNE_CACHE");
   if (!path) return false;
   std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -143,9 +149,135 @@ bool autotune_lookup(int64_t n, evd_job_t job, evd_prec_t prec, int* b, int* nb)
     if (e.bucket == bucket_of(n) && e.job == (int)job && e.prec == (int)prec) {
       *b = e.b;
       *nb = e.nb;
+      if (bc_per_sm) *bc_per_sm = e.bc_per_sm;
       return true;
     }
   return false;
+}
+
+// ---------------------------------------------------------------- graph path
+// The whole batch as one CUDA graph: every problem's solve (a plan each, its D&C in
+// the sync-free form) is captured on its lane's stream, the lanes forked from and
+// joined back to one origin stream, and the graph launched once.  The instantiated
+// graph and its plans are kept: a call with exactly the same arguments (sizes,
+// pointers, workspace, device) launches it again without capturing.
+struct BatchGraph {
+  std::vector<int64_t> key;
+  std::vector<evd_plan_t> plans;
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t start = nullptr, before = nullptr, after = nullptr;
+  cudaStream_t origin = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void release() {
+    if (origin) cudaStreamSynchronize(origin);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto p : plans) evd_plan_destroy(p);
+    for (auto e : done) if (e) cudaEventDestroy(e);
+    for (auto l : lanes) if (l) cudaStreamDestroy(l);
+    if (start) cudaEventDestroy(start);
+    if (before) cudaEventDestroy(before);
+    if (after) cudaEventDestroy(after);
+    if (origin) cudaStreamDestroy(origin);
+    *this = BatchGraph();
+  }
+};
+std::mutex g_graph_mu;
+BatchGraph g_batch;
+std::atomic<bool> g_last_graph{false};
+
+evd_status_t batched_graph(const Assignment& a, int count, const int64_t* n_host, double* const* A_host,
+                           const int64_t* lda_host, double* const* w_host, double* const* Q_host,
+                           const int64_t* ldq_host, evd_job_t job, void* ws, size_t ws_bytes, cudaStream_t caller,
+                           int dev, bool* captured) {
+  *captured = false;
+  std::vector<int64_t> key = {count, (int64_t)job, (int64_t)(uintptr_t)ws, (int64_t)ws_bytes, dev};
+  for (int i = 0; i < count; ++i) {
+    key.push_back(n_host[i]);
+    key.push_back(lda_host[i]);
+    key.push_back((int64_t)(uintptr_t)A_host[i]);
+    key.push_back((int64_t)(uintptr_t)w_host[i]);
+    key.push_back(job == EVD_VECTORS ? (int64_t)(uintptr_t)Q_host[i] : 0);
+    key.push_back(job == EVD_VECTORS ? ldq_host[i] : 0);
+  }
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  BatchGraph& g = g_batch;
+  if (!(g.exec && g.key == key)) {
+    g.release();
+    auto fail = [&]() {
+      g.release();
+      (void)cudaGetLastError();
+      return EVD_OK;  // not captured: the caller runs the live lanes
+    };
+    if (cudaStreamCreateWithFlags(&g.origin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.before, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.after, cudaEventDisableTiming) != cudaSuccess)
+      return fail();
+    g.lanes.assign(a.lanes, nullptr);
+    g.done.assign(a.lanes, nullptr);
+    for (int l = 0; l < a.lanes; ++l)
+      if (cudaStreamCreateWithFlags(&g.lanes[l], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&g.done[l], cudaEventDisableTiming) != cudaSuccess)
+        return fail();
+    // plans (allocations happen here, before the capture)
+    g.plans.assign(count, nullptr);
+    for (int l = 0; l < a.lanes; ++l)
+      for (int i : a.items[l]) {
+        const evd_status_t s = evd_plan_create(&g.plans[i], n_host[i], lda_host[i], job, EVD_FP64, 0, 0, g.lanes[l]);
+        if (s != EVD_OK) {
+          g.release();
+          return s;
+        }
+        plan_set_sync_free(g.plans[i], true);
+        evd_plan_set_option(g.plans[i], EVD_OPT_ORDER, 0);
+      }
+    if (cudaStreamBeginCapture(g.origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) return fail();
+    evd_status_t serr = EVD_OK;
+    bool cerr = cudaEventRecord(g.start, g.origin) != cudaSuccess;
+    for (int l = 0; l < a.lanes && !cerr && serr == EVD_OK; ++l) {
+      cerr = cudaStreamWaitEvent(g.lanes[l], g.start, 0) != cudaSuccess;
+      void* wsl = static_cast<char*>(ws) + a.ws_offset[l];
+      for (int i : a.items[l]) {
+        if (cerr || serr != EVD_OK) break;
+        serr = evd_syevd(g.plans[i], A_host[i], w_host[i], job == EVD_VECTORS ? Q_host[i] : nullptr,
+                         job == EVD_VECTORS ? ldq_host[i] : 1, wsl);
+      }
+      if (!cerr && serr == EVD_OK)
+        cerr = cudaEventRecord(g.done[l], g.lanes[l]) != cudaSuccess ||
+               cudaStreamWaitEvent(g.origin, g.done[l], 0) != cudaSuccess;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(g.origin, &graph);
+    g.graph = graph;
+    if (serr == EVD_ERR_INVALID_ARG || serr == EVD_ERR_WORKSPACE || serr == EVD_ERR_OOM) {
+      g.release();
+      (void)cudaGetLastError();
+      *captured = true;  // a host-side error of the solve itself: report it, no fallback
+      return serr;
+    }
+    if (cerr || serr != EVD_OK || ec != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess)
+      return fail();
+    g.key = key;
+  }
+  *captured = true;
+  // after the caller's earlier work, and the caller after the graph
+  EVD_CUDA_TRY(cudaEventRecord(g.before, caller));
+  EVD_CUDA_TRY(cudaStreamWaitEvent(g.origin, g.before, 0));
+  EVD_CUDA_TRY(cudaGraphLaunch(g.exec, g.origin));
+  EVD_CUDA_TRY(cudaEventRecord(g.after, g.origin));
+  EVD_CUDA_TRY(cudaStreamWaitEvent(caller, g.after, 0));
+  EVD_CUDA_TRY(cudaStreamSynchronize(g.origin));
+  evd_status_t st_all = EVD_OK;
+  for (int i = 0; i < count; ++i) {
+    int info = 0;
+    const evd_status_t s = evd_plan_status(g.plans[i], &info);
+    if (st_all == EVD_OK && s != EVD_OK) st_all = s;
+  }
+  return st_all;
 }
 
 }  // namespace evd
@@ -166,20 +298,33 @@ evd_status_t evd_batched_workspace_size(int count, const int64_t* n_host, evd_jo
   return EVD_OK;
 }
 
+int evd_batched_last_graph(void) { return g_last_graph.load() ? 1 : 0; }
+
 evd_status_t evd_syevd_batched(int count, const int64_t* n_host, double* const* A_host, const int64_t* lda_host,
                                double* const* w_host, double* const* Q_host, const int64_t* ldq_host, evd_job_t job,
                                void* ws, size_t ws_bytes, void* stream) {
   if (count < 0 || (count > 0 && (!n_host || !A_host || !lda_host || !w_host))) return EVD_ERR_INVALID_ARG;
   if (job == EVD_VECTORS && count > 0 && (!Q_host || !ldq_host)) return EVD_ERR_INVALID_ARG;
   if (count == 0) return EVD_OK;
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count; ++i) {
     if (n_host[i] < 0 || lda_host[i] < std::max<int64_t>(1, n_host[i])) return EVD_ERR_INVALID_ARG;
+    if (job == EVD_VECTORS && ldq_host[i] < std::max<int64_t>(1, n_host[i])) return EVD_ERR_INVALID_ARG;
+  }
   Assignment a;
   evd_status_t st = assign(count, n_host, nullptr, job, &a);
   if (st != EVD_OK) return st;
   if (!ws || ws_bytes < a.total || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return EVD_ERR_WORKSPACE;
   int dev = 0;
   EVD_CUDA_TRY(cudaGetDevice(&dev));
+  {
+    bool captured = false;
+    st = batched_graph(a, count, n_host, A_host, lda_host, w_host, Q_host, ldq_host, job, ws, ws_bytes,
+                       static_cast<cudaStream_t>(stream), dev, &captured);
+    g_last_graph.store(captured);
+    if (captured) return st;
+    // the capture itself was refused (for example a driver without cooperative
+    // launches in graphs): run the same work on live lanes instead
+  }
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   std::vector<cudaStream_t> lanes(a.lanes, nullptr);
   std::vector<cudaEvent_t> done(a.lanes, nullptr);
@@ -255,7 +400,16 @@ evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char*
     *nb = 32;
     return EVD_OK;
   }
-  static const int cand[][2] = {{32, 32}, {32, 64}, {32, 128}, {64, 64}, {64, 128}, {128, 128}};
+  if (n > 65535) return EVD_ERR_NOT_SUPPORTED;  // the fill kernel's grid.y = n
+  // candidates: b in {32, 64, 128}, nb = b, 2b, ..., 16b (nb below n).  From
+  // n = 32768 on only b = 64 is tried: the fused BC-Back waves exist for b = 64 and
+  // the other widths take the batched BC-Back, several times slower at that size.
+  std::vector<std::pair<int, int>> cand;
+  for (int bb : {32, 64, 128}) {
+    if (bb >= n || (n >= 32768 && bb != 64)) continue;
+    for (int f = 1; f <= 16; f *= 2)
+      if ((int64_t)bb * f < n) cand.push_back({bb, bb * f});
+  }
   double* A = nullptr;
   double* A0 = nullptr;
   double* w = nullptr;
@@ -276,31 +430,31 @@ evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char*
     release();
     return EVD_ERR_OOM;
   }
-  if (n > 65535) { release(); return EVD_ERR_NOT_SUPPORTED; }  // the fill kernel's grid.y = n
   k_fill_symmetric<<<dim3((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)n), 256>>>(A0, n, 16174);
   count_launch();
   if (cudaGetLastError() != cudaSuccess) { release(); return EVD_ERR_CUDA; }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  double best = 1e300;
-  int bb = 0, bnb = 0;
   evd_status_t err = EVD_OK;
-  for (const auto& c : cand) {
-    if (c[0] >= n) continue;
+  bool warmed = false;
+  // one timed solve of (b, nb, bc_per_sm); the first solve of the call is an
+  // untimed warm-up
+  auto time_one = [&](int bb, int nbb, int per_sm, double* ms_out) -> bool {
     evd_plan_t p = nullptr;
-    if (evd_plan_create(&p, n, n, job, prec, c[0], c[1], nullptr) != EVD_OK) continue;
+    if (evd_plan_create(&p, n, n, job, prec, bb, nbb, nullptr) != EVD_OK) return false;
+    evd_plan_set_option(p, EVD_OPT_BC_CTAS_PER_SM, per_sm);
     size_t need = 0;
     evd_plan_workspace_size(p, &need);
     if (need > ws_cap) {
       if (ws) cudaFree(ws);
       ws = nullptr;
-      if (cudaMalloc(&ws, need) != cudaSuccess) { evd_plan_destroy(p); err = EVD_ERR_OOM; break; }
+      ws_cap = 0;
+      if (cudaMalloc(&ws, need) != cudaSuccess) { evd_plan_destroy(p); err = EVD_ERR_OOM; return false; }
       ws_cap = need;
     }
-    double ms_c = 0.0;
     bool ok = true;
-    for (int rep = 0; rep < 2 && ok; ++rep) {  // one untimed warm-up, one timed solve
+    for (int rep = warmed ? 1 : 0; rep < 2 && ok; ++rep) {
       cudaMemcpyAsync(A, A0, mat, cudaMemcpyDeviceToDevice, nullptr);
       cudaEventRecord(e0, nullptr);
       ok = evd_syevd(p, A, w, Q, n, ws) == EVD_OK;
@@ -309,13 +463,28 @@ evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char*
       ok = ok && evd_plan_status(p, &info) == EVD_OK;
       float t = 0;
       cudaEventElapsedTime(&t, e0, e1);
-      ms_c = t;
+      *ms_out = t;
     }
+    warmed = true;
     evd_plan_destroy(p);
-    if (ok && ms_c < best) {
-      best = ms_c;
-      bb = c[0];
-      bnb = c[1];
+    return ok;
+  };
+  double best = 1e300;
+  int bb = 0, bnb = 0, bper = 0;
+  for (const auto& c : cand) {
+    double ms_c = 0.0;
+    if (!time_one(c.first, c.second, 0, &ms_c)) {
+      if (err != EVD_OK) break;
+      continue;
+    }
+    if (ms_c < best) { best = ms_c; bb = c.first; bnb = c.second; }
+  }
+  // sweep grouping of the bulge chasing: one or two sweeps in flight per SM
+  if (err == EVD_OK && bb > 0) {
+    for (int per_sm : {1, 2}) {
+      double ms_c = 0.0;
+      if (time_one(bb, bnb, per_sm, &ms_c) && ms_c < best) { best = ms_c; bper = per_sm; }
+      if (err != EVD_OK) break;
     }
   }
   cudaEventDestroy(e0);
@@ -328,7 +497,9 @@ evd_status_t evd_autotune(int64_t n, evd_job_t job, evd_prec_t prec, const char*
   if (cache_path) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     std::vector<CacheEntry> v = read_cache(cache_path);
-    v.push_back({bucket_of(n), (int)job, (int)prec, bb, bnb, best});
+    CacheEntry ce{bucket_of(n), (int)job, (int)prec, bb, bnb, best};
+    ce.bc_per_sm = bper;
+    v.push_back(ce);
     write_cache(cache_path, v);
   }
   return EVD_OK;

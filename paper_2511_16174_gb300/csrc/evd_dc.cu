@@ -501,6 +501,28 @@ __global__ void k_dc_copy_back(const MergeDesc* md, const double* vals, double* 
     Q[(off + r) + (off + c) * ldq] = Qs[(off + r) + (off + c) * lds];
 }
 
+// Sync-free merges (no host read of k): the product runs over the whole merge, so
+// the columns of Qn past the k nondeflated ones and U past its k x k block must be
+// zero (stale values there, even non-finite ones, would otherwise reach the first k
+// columns of the product).
+__global__ void k_dc_pad_zero(const MergeDesc* md, const int* kk, double* Qn, double* U, int64_t ld) {
+  const MergeDesc M = md[blockIdx.z];
+  const int64_t off = M.off, m = M.n1 + M.n2;
+  const int k = kk[blockIdx.z];
+  const int64_t c = blockIdx.y;
+  if (c >= m) return;
+  double* qc = Qn + off + (off + c) * ld;
+  double* uc = U + off + (off + c) * ld;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+    if (c >= k) {
+      qc[r] = 0.0;
+      uc[r] = 0.0;
+    } else if (r >= k) {
+      uc[r] = 0.0;
+    }
+  }
+}
+
 __global__ void k_zero_cols(double* Q, int64_t ldq, int64_t n, int64_t j0) {
   int64_t j = j0 + blockIdx.y;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -519,14 +541,57 @@ void build_tree(int64_t off, int64_t n, int depth, std::vector<std::vector<Merge
 
 }  // namespace
 
+// The merge tree of order n: descriptors level by level, deepest first (the order
+// dc_run walks them), and the leaves.  It depends on n only.
+void dc_tree(int64_t n, std::vector<MergeDesc>& all, std::vector<size_t>& lvl_start, std::vector<int64_t>& loff,
+             std::vector<int>& ln) {
+  std::vector<std::vector<MergeDesc>> levels;
+  build_tree(0, n, 0, levels, loff, ln);
+  for (int L = (int)levels.size() - 1; L >= 0; --L) {
+    lvl_start.push_back(all.size());
+    for (auto& m : levels[L]) all.push_back(m);
+  }
+  lvl_start.push_back(all.size());
+}
+
+
+size_t dc_tree_bytes(int64_t n) {
+  if (n <= 0) return 256;
+  std::vector<MergeDesc> all;
+  std::vector<size_t> lvl;
+  std::vector<int64_t> loff;
+  std::vector<int> ln;
+  dc_tree(n, all, lvl, loff, ln);
+  return align_up(sizeof(MergeDesc) * (all.size() + 1), 256) + align_up(sizeof(int64_t) * loff.size(), 256) +
+         align_up(sizeof(int) * ln.size(), 256);
+}
+
+evd_status_t dc_tree_upload(int64_t n, void* dst, size_t bytes) {
+  if (n <= 0) return EVD_OK;
+  std::vector<MergeDesc> all;
+  std::vector<size_t> lvl;
+  std::vector<int64_t> loff;
+  std::vector<int> ln;
+  dc_tree(n, all, lvl, loff, ln);
+  if (bytes < dc_tree_bytes(n)) return EVD_ERR_INVALID_ARG;
+  char* p = static_cast<char*>(dst);
+  const size_t a = align_up(sizeof(MergeDesc) * (all.size() + 1), 256), b = align_up(sizeof(int64_t) * loff.size(), 256);
+  if (!all.empty()) EVD_CUDA_TRY(cudaMemcpy(p, all.data(), sizeof(MergeDesc) * all.size(), cudaMemcpyHostToDevice));
+  EVD_CUDA_TRY(cudaMemcpy(p + a, loff.data(), sizeof(int64_t) * loff.size(), cudaMemcpyHostToDevice));
+  EVD_CUDA_TRY(cudaMemcpy(p + a + b, ln.data(), sizeof(int) * ln.size(), cudaMemcpyHostToDevice));
+  return EVD_OK;
+}
+
+
 evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t ldq, const DcWork& w) {
   const int64_t n = pc.n;
   cudaStream_t s = pc.stream;
   if (n == 0) return EVD_OK;
-  std::vector<std::vector<MergeDesc>> levels;
+  std::vector<MergeDesc> all;
+  std::vector<size_t> lvl_start;
   std::vector<int64_t> loff;
   std::vector<int> ln;
-  build_tree(0, n, 0, levels, loff, ln);
+  dc_tree(n, all, lvl_start, loff, ln);
   // vector scratch (DcWork::vec holds 10 n doubles, DcWork::ivec 32 n ints)
   double* ds = w.vec;
   double* zs = w.vec + n;
@@ -546,13 +611,6 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
   int* rank = w.ivec + 6 * n;
   int* pos = w.ivec + 7 * n;
   // merge descriptors and per-merge scalars
-  std::vector<MergeDesc> all;
-  std::vector<size_t> lvl_start;
-  for (int L = (int)levels.size() - 1; L >= 0; --L) {
-    lvl_start.push_back(all.size());
-    for (auto& m : levels[L]) all.push_back(m);
-  }
-  lvl_start.push_back(all.size());
   const size_t nmerge = all.size(), nleaves = loff.size();
   char* meta = reinterpret_cast<char*>(w.ivec + 8 * n);
   size_t mb = 0;
@@ -566,9 +624,19 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
   int* d_nrot = reinterpret_cast<int*>(carve(sizeof(int) * (nmerge + 1)));
   int* d_grp = reinterpret_cast<int*>(carve(sizeof(int) * 2 * (nmerge + 1)));
   if (mb > ((size_t)24 * n + 1024) * sizeof(int)) return ws_fail("dc merge descriptors", ((size_t)24 * n + 1024) * sizeof(int), mb);
-  if (nmerge) EVD_CUDA_TRY(cudaMemcpyAsync(d_md, all.data(), sizeof(MergeDesc) * nmerge, cudaMemcpyHostToDevice, s));
-  EVD_CUDA_TRY(cudaMemcpyAsync(d_loff, loff.data(), sizeof(int64_t) * nleaves, cudaMemcpyHostToDevice, s));
-  EVD_CUDA_TRY(cudaMemcpyAsync(d_ln, ln.data(), sizeof(int) * nleaves, cudaMemcpyHostToDevice, s));
+  if (pc.dc_tree) {
+    // the plan's resident copy of the tree (uploaded once, at plan creation)
+    char* t = static_cast<char*>(pc.dc_tree);
+    d_md = reinterpret_cast<MergeDesc*>(t);
+    d_loff = reinterpret_cast<int64_t*>(t + align_up(sizeof(MergeDesc) * (nmerge + 1), 256));
+    d_ln = reinterpret_cast<int*>(t + align_up(sizeof(MergeDesc) * (nmerge + 1), 256) +
+                                  align_up(sizeof(int64_t) * nleaves, 256));
+  } else {
+    if (pc.dc_sync_free) return EVD_ERR_INVALID_ARG;  // a captured solve cannot copy from transient host memory
+    if (nmerge) EVD_CUDA_TRY(cudaMemcpyAsync(d_md, all.data(), sizeof(MergeDesc) * nmerge, cudaMemcpyHostToDevice, s));
+    EVD_CUDA_TRY(cudaMemcpyAsync(d_loff, loff.data(), sizeof(int64_t) * nleaves, cudaMemcpyHostToDevice, s));
+    EVD_CUDA_TRY(cudaMemcpyAsync(d_ln, ln.data(), sizeof(int) * nleaves, cudaMemcpyHostToDevice, s));
+  }
   // Q = 0, tears, leaves
   for (int64_t j0 = 0; j0 < n; j0 += 65535) {
     int64_t cols = n - j0 < 65535 ? n - j0 : 65535;
@@ -599,12 +667,17 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
                                                                                  rots, w.Qtmp, n); count_launch();
     EVD_CUDA_TRY(cudaGetLastError());
     }
-    // the number of nondeflated roots sizes the products: read it on the host
-    EVD_CUDA_TRY(cudaMemcpyAsync(hk.data(), d_k + b0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
-    EVD_CUDA_TRY(cudaMemcpyAsync(hg.data(), d_grp + 2 * b0, sizeof(int) * 2 * cnt, cudaMemcpyDeviceToHost, s));
-    EVD_CUDA_TRY(cudaStreamSynchronize(s));
+    // the number of nondeflated roots sizes the products: read it on the host, or,
+    // sync-free, size every grid and product by the merge itself
     int kmax = 0;
-    for (size_t q = 0; q < cnt; ++q) kmax = std::max(kmax, hk[q]);
+    if (pc.dc_sync_free) {
+      kmax = (int)mmax;
+    } else {
+      EVD_CUDA_TRY(cudaMemcpyAsync(hk.data(), d_k + b0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+      EVD_CUDA_TRY(cudaMemcpyAsync(hg.data(), d_grp + 2 * b0, sizeof(int) * 2 * cnt, cudaMemcpyDeviceToHost, s));
+      EVD_CUDA_TRY(cudaStreamSynchronize(s));
+      for (size_t q = 0; q < cnt; ++q) kmax = std::max(kmax, hk[q]);
+    }
     if (kmax > 0) {
       k_dc_gather_nd<<<dim3(rx, (unsigned)kmax, (unsigned)cnt), 256, 0, s>>>(md, d_k + b0, ndl, pos, ds, zs, dl, zl,
                                                                              w.Qtmp, n, w.Qn); count_launch();
@@ -615,10 +688,30 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
       k_dc_vectors<<<dim3(kx, (unsigned)cnt), 128, 0, s>>>(md, d_k + b0, dl, org, tau, zh, pos, w.Umat, n); count_launch();
       EVD_CUDA_TRY(cudaGetLastError());
       }
+      if (pc.dc_sync_free) {
+        // X = Qn U over the whole merge block, Qn and U zero past the k nondeflated
+        // columns (and rows of U); X's columns from k on are not read
+        k_dc_pad_zero<<<dim3(rx, (unsigned)mmax, (unsigned)cnt), 256, 0, s>>>(md, d_k + b0, w.Qn, w.Umat, n); count_launch();
+        EVD_CUDA_TRY(cudaGetLastError());
+        for (size_t q = 0; q < cnt; ++q) {
+          const MergeDesc& M = all[b0 + q];
+          const int64_t off = M.off, m = M.n1 + M.n2;
+          Gemm g;
+          g.tag = "dc_merge_gemm";
+          g.status = pc.status;
+          g.m = m; g.n = m; g.k = m;
+          g.A = w.Qn + off + off * n; g.lda = n;
+          g.B = w.Umat + off + off * n; g.ldb = n;
+          g.C = Q + off + off * ldq; g.ldc = ldq;
+          g.alpha = 1.0; g.beta = 0.0;
+          evd_status_t st = gemm(g, pc.ref_slices, w.gemm_ws, w.gemm_ws_bytes, s);
+          if (st != EVD_OK) return st;
+        }
+      }
       // X = Qn U into the first k columns of the block of Q (the block is free now),
       // as X(0:n1, :) = Qn(0:n1, 0:c1+c2) U(0:c1+c2, :) and
       //    X(n1:m, :) = Qn(n1:m, c1:k)     U(c1:k, :)
-      for (size_t q = 0; q < cnt; ++q) {
+      for (size_t q = 0; q < cnt && !pc.dc_sync_free; ++q) {
         const int k = hk[q];
         if (k == 0) continue;
         const MergeDesc& M = all[b0 + q];

@@ -101,6 +101,8 @@ struct PlanCore {
   int bc_ctas_per_sm = 0; // bulge-chasing CTAs (sweeps in flight) per SM, 0 = by the sweep count
   int xe_slices = 4;      // slices of the refinement's X E product (E is at the error level)
   int order = -1;         // back transformation: 0 conventional, 1 reordered (Sec. 3.3), -1 by size
+  bool dc_sync_free = false;  // D&C without host reads (capturable in a CUDA graph)
+  void* dc_tree = nullptr;    // device copy of the D&C merge tree (plan-owned), or nullptr
   int* status = nullptr;  // device int[kStatusWords]
 };
 
@@ -133,11 +135,13 @@ struct BcWork {
   unsigned* bar;
 };
 int64_t bc_num_reflectors(int64_t n, int b);
+// Switch a plan's D&C to its sync-free form (no host reads; evd_api.cu).
+void plan_set_sync_free(evd_plan_t p, bool on);
 // Plan tunables and workspace size without creating a plan (evd_api.cu).
 void fill_core(PlanCore& c, int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb);
 size_t plan_workspace_bytes(int64_t n, int64_t lda, evd_job_t job, evd_prec_t prec, int b, int nb);
 // Autotuner cache lookup for plans created with b = nb = 0 (evd_batched.cu).
-bool autotune_lookup(int64_t n, evd_job_t job, evd_prec_t prec, int* b, int* nb);
+bool autotune_lookup(int64_t n, evd_job_t job, evd_prec_t prec, int* b, int* nb, int* bc_per_sm);
 // Upper bound on the number of reflector groups in one BC-Back wave (groups of a
 // wave start 2b rows apart, all below row n).
 int64_t bc_wave_max_groups(int64_t n, int b);
@@ -154,6 +158,10 @@ struct DcWork {
 };
 evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t ldq,
                     const DcWork& w);
+// Bytes of the device copy of the D&C merge tree of order n, and its upload
+// (synchronous; done once per plan).
+size_t dc_tree_bytes(int64_t n);
+evd_status_t dc_tree_upload(int64_t n, void* dst, size_t bytes);
 
 constexpr int kSbrBackPanels = 16;  // SBR panels merged into one compact WY group in SBR-Back
 struct BackWork {

@@ -56,6 +56,13 @@ StatScope::StatScope(const char* cat, cudaStream_t s, double flops, double bytes
     : cat_(cat), engine_(engine), s_(s) {
   on_ = g_on.load(std::memory_order_relaxed);
   if (!on_) return;
+  // no timing events inside a stream capture (a captured solve is timed as a whole)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    on_ = false;
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   a_ = take_event();
   cudaEventRecord(static_cast<cudaEvent_t>(a_), s_);

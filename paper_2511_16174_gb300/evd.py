@@ -57,6 +57,7 @@ _SIGS = {
                    _int, _vp, _sz, _vp], _int),
     "evd_dgemm_static": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp,
                           _i64, _int, _vp], _int),
+    "evd_batched_last_graph": ([], _int),
     "evd_autotune": ([_i64, _int, _int, ctypes.c_char_p, ctypes.POINTER(_int), ctypes.POINTER(_int)], _int),
     "evd_stats_enable": ([_int], None),
     "evd_stats_reset": ([], None),
@@ -257,6 +258,38 @@ def syevd_batched(As, job="V", stream=None):
     _check(_lib.evd_syevd_batched(count, ns, Ap, lds, wp, Qp, ldq, jb, _ptr(ws), sz.value, _stream_ptr(stream)),
            "evd_syevd_batched")
     return ws_list, Qs
+
+
+class Batch:
+    """Fixed buffers for repeated batched solves of the same sizes: inputs A[i]
+    (column-major, overwritten by each run), outputs w[i], Q[i], one workspace.  A
+    run with the same buffers replays the library's captured graph."""
+
+    def __init__(self, sizes, job="V", device="cuda"):
+        self.sizes = [int(n) for n in sizes]
+        self.job = EVD_VECTORS if job == "V" else EVD_VALUES
+        cnt = len(self.sizes)
+        self.A = [empty_colmajor(n, n, device=device) for n in self.sizes]
+        self.w = [torch.empty(n, dtype=torch.float64, device=device) for n in self.sizes]
+        self.Q = [empty_colmajor(n, n, device=device) for n in self.sizes] if self.job == EVD_VECTORS else [None] * cnt
+        self._n = (_i64 * cnt)(*self.sizes)
+        self._ld = (_i64 * cnt)(*[max(1, n) for n in self.sizes])
+        sz = _sz()
+        _check(_lib.evd_batched_workspace_size(cnt, self._n, self.job, ctypes.byref(sz)), "evd_batched_workspace_size")
+        self.ws_bytes = sz.value
+        self.ws = torch.empty(max(sz.value, 256), dtype=torch.uint8, device=device)
+        self._Ap = (_vp * cnt)(*[a.data_ptr() for a in self.A])
+        self._wp = (_vp * cnt)(*[w.data_ptr() for w in self.w])
+        self._Qp = (_vp * cnt)(*[(q.data_ptr() if q is not None else 0) for q in self.Q])
+
+    def run(self, stream=None):
+        _check(_lib.evd_syevd_batched(len(self.sizes), self._n, self._Ap, self._ld, self._wp, self._Qp, self._ld,
+                                      self.job, _ptr(self.ws), self.ws_bytes, _stream_ptr(stream)),
+               "evd_syevd_batched")
+
+
+def batched_last_graph():
+    return bool(_lib.evd_batched_last_graph())
 
 
 def autotune(n, job="V", prec="fp64", cache_path=None):

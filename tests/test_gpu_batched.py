@@ -1,8 +1,9 @@
 """Batched solve and the (b, nb) autotuner, through the C ABI.
 
-* Uneven batch (sizes from 1 to 1030, longest-first over concurrent lanes): every
-  matrix's eigenvalues agree with the oracle within the acceptance bound, and every
-  Q meets the orthogonality and residual bounds.
+* Uneven batch (sizes from 1 to 1030, longest-first over lanes), run as one captured
+  CUDA graph: every matrix's eigenvalues agree with the oracle within the acceptance
+  bound, and every Q meets the orthogonality and residual bounds.  A second run with
+  the same buffers replays the graph and gives the same results bit for bit.
 * Autotuner: returns a candidate pair, writes it to the JSON cache, answers the
   second call from the cache, and a plan created with b = nb = 0 picks the cached
   pair when EVD_AUTOTUNE_CACHE names the file.
@@ -32,17 +33,22 @@ def evd():
 def test_batched_uneven_sizes_match_oracle(evd):
     sizes = [3, 17, 64, 100, 257, 300, 513, 600, 1030, 40, 8, 1, 129, 700]
     mats = [inputs.goe(n, 8000 + i) for i, n in enumerate(sizes)]
-    As = []
-    for A in mats:
-        t = evd.empty_colmajor(A.shape[0], A.shape[0])
-        t.copy_(torch.from_numpy(A))
-        As.append(t)
-    ws, Qs = evd.syevd_batched(As, job="V")
-    torch.cuda.synchronize()
-    for A, w, Q in zip(mats, ws, Qs):
+    batch = evd.Batch(sizes, job="V")
+    results = []
+    for rep in range(2):
+        for A, t in zip(mats, batch.A):
+            t.copy_(torch.from_numpy(A))
+        batch.run()
+        torch.cuda.synchronize()
+        assert evd.batched_last_graph()
+        results.append(([w.cpu().numpy() for w in batch.w], [q.cpu().numpy() for q in batch.Q]))
+    for i in range(len(sizes)):
+        assert np.array_equal(results[0][0][i], results[1][0][i])
+        assert np.array_equal(results[0][1][i], results[1][1][i])
+    for A, w, Q in zip(mats, results[1][0], results[1][1]):
         n = A.shape[0]
         w_ref, _ = oracle.eigh(A, want_vectors=False) if n > 8 else oracle.jacobi(A)
-        m = oracle.metrics(A, w.cpu().numpy(), Q.cpu().numpy(), w_ref=np.sort(w_ref))
+        m = oracle.metrics(A, w, Q, w_ref=np.sort(w_ref))
         acc = oracle.acceptance(n, float(np.max(np.abs(w_ref))) if n else 0.0)
         assert m["dlam"] <= acc["dlam"], (n, m)
         assert m["orth_max"] <= acc["orth_max"], (n, m)

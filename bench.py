@@ -482,7 +482,8 @@ def profile_target(args):
         lam = np.sort(spectrum_for(n, inputs.SEED_BASE + 1))
         A = evd.as_colmajor(torch.from_numpy(inputs.qlq(lam, inputs.SEED_BASE + 1)).cuda()) if n <= 8192 else \
             evd.as_colmajor(inputs.qlq_device(lam, inputs.SEED_BASE + 1))
-        evd.syevd(A, job="V", prec=args.prec, b=args.b, nb=args.nb)
+        options = {"order": args.order} if args.order is not None else None
+        evd.syevd(A, job="V", prec=args.prec, b=args.b, nb=args.nb, options=options)
     torch.cuda.synchronize()
     print("profile target done", flush=True)
     return 0

@@ -33,7 +33,6 @@ struct WsLayout {
   int64_t ldx = 0;
   char* bb_scratch = nullptr;
   size_t bb_bytes = 0;
-  int2* ranges = nullptr;
   // union region
   char* uni = nullptr;
   size_t uni_bytes = 0;
@@ -48,6 +47,7 @@ struct evd_plan_s {
   unsigned* d_bar = nullptr; // 2 words
   int* d_prog = nullptr;     // n ints
   void* d_tree = nullptr;    // the D&C merge tree (uploaded once)
+  BbSchedule* bb = nullptr;  // the fused BC-Back schedule (b = 64, n >= 1024, vectors)
   bool own_stream = false;
   // reordered stages: BC-Back of the identity on a high-priority stream and D&C on a
   // low-priority one, forked from and joined back to the plan's stream with events
@@ -132,7 +132,6 @@ WsLayout make_layout(const PlanCore& pc, void* ws) {
     L.Xsb = c.take<double>((size_t)L.ldx * n);
     L.bb_bytes = bcback_fused_scratch_bytes(n, b, pc.ref_slices);
     L.bb_scratch = c.take<char>(L.bb_bytes);
-    L.ranges = c.take<int2>((size_t)std::max<int64_t>(bc_num_groups(n, b), 1));
   }
   size_t ub = std::max({sbr_union_bytes(n, b, pc.nb), dc_union_bytes(n), back_union_bytes(n, b),
                         pc.prec == EVD_SPLIT_BF16 ? refine_union_bytes(n) : (size_t)0});
@@ -344,6 +343,19 @@ evd_status_t evd_plan_create(evd_plan_t* plan, int64_t n, int64_t lda, evd_job_t
     return EVD_ERR_CUDA;
   }
   c.dc_tree = p->d_tree;
+  if (job == EVD_VECTORS && c.b == 64 && n >= 1024) {
+    p->bb = new (std::nothrow) BbSchedule();
+    if (!p->bb) {
+      evd_plan_destroy(p);
+      return EVD_ERR_OOM;
+    }
+    const evd_status_t bst = bb_schedule_build(n, c.b, p->bb);
+    if (bst != EVD_OK) {
+      evd_plan_destroy(p);
+      return bst;
+    }
+    c.bb = p->bb;
+  }
   cudaMemset(p->d_status, 0, sizeof(int) * kStatusWords);
   cudaMemset(p->d_bar, 0, sizeof(unsigned) * 4);
   c.status = p->d_status;
@@ -547,7 +559,7 @@ evd_status_t reordered_back(evd_plan_t p, const WsLayout& L, const double* A, do
   BackWork bw;
   bw.gemm_ws = L.bb_scratch;
   bw.gemm_ws_bytes = L.bb_bytes;
-  st = bc_back_run(ch, bc_work(p, L), L.Xsb, L.ldx, bw, L.ranges);
+  st = bc_back_run(ch, bc_work(p, L), L.Xsb, L.ldx, bw, true);
   dc_thread.join();
   // join whatever both streams queued, even after an error, so that the order holds
   cudaEventRecord(p->ev_join_hi, p->hi);
@@ -631,6 +643,10 @@ void evd_plan_destroy(evd_plan_t p) {
   cudaFree(p->d_bar);
   cudaFree(p->d_prog);
   cudaFree(p->d_tree);
+  if (p->bb) {
+    bb_schedule_free(p->bb);
+    delete p->bb;
+  }
   delete p;
 }
 

@@ -181,10 +181,127 @@ int64_t bc_num_groups(int64_t n, int b) {
   return total;
 }
 
+// The wave launches of the fused BC-Back in order (wave t, then the maximal runs of
+// valid groups of that wave), each group's (J, k), and the identity start's column
+// ranges.  Identity start: X = I at first, so row r is nonzero in column r only; a
+// group mixes its rows, so afterwards all of them are nonzero at most over the union
+// of their column ranges.  With g = b the group G(J, k) covers rows (J+k) b + 1 ..
+// (J+k+2) b - 1, inside the b-row blocks q = J + k and q + 1 (block q: rows q b + 1
+// .. q b + b), and the groups of one launch cover disjoint blocks, so tracking one
+// column interval per block, in launch order, gives a superset of every group's
+// support.
+evd_status_t bb_schedule_build(int64_t n, int b, BbSchedule* out) {
+  BbSchedule sc;
+  const int g = b, h = g + b - 1;
+  const int64_t nJ = ceil_div(n - 2, g);
+  auto kc = [&](int64_t J) { return sweep_steps_b(n, b, J * g); };
+  const int64_t tmax = kc(0) + nJ - 2;
+  const int64_t nblk = n / b + 3;
+  std::vector<int64_t> cmin(nblk), cmax(nblk);
+  for (int64_t q = 0; q < nblk; ++q) {
+    cmin[q] = std::min<int64_t>(q * b + 1, n - 1);
+    cmax[q] = std::min<int64_t>(q * b + b, n - 1);
+  }
+  std::vector<int2> gjk, ranges;
+  for (int64_t t = 0; t <= tmax; ++t) {
+    int64_t jp = std::min<int64_t>(t, nJ - 1);
+    while (jp >= 0) {
+      if (t - jp >= kc(nJ - 1 - jp)) { --jp; continue; }
+      const int64_t jhi = jp;
+      while (jp >= 0 && t - jp < kc(nJ - 1 - jp)) --jp;
+      const int64_t jlo = jp + 1;
+      BbLaunch L;
+      L.count = (int)(jhi - jlo + 1);
+      // group 0 (J' = jlo) is the lowest group of the run and the only one that may reach row n
+      L.R0 = (nJ - 1 - jlo) * g + 1 + (t - jlo) * b;
+      L.hh0 = (int)std::min<int64_t>(h, n - L.R0);
+      L.g0 = (int64_t)gjk.size();
+      L.tile0 = INT64_MAX;
+      L.tile1 = -1;
+      L.work_tiles = 0;
+      for (int64_t jq = jlo; jq <= jhi; ++jq) {
+        const int64_t J = nJ - 1 - jq, k = t - jq, q = J + k;
+        gjk.push_back(make_int2((int)J, (int)k));
+        const int64_t lo = std::min(cmin[q], cmin[q + 1]), hi = std::max(cmax[q], cmax[q + 1]);
+        cmin[q] = cmin[q + 1] = lo;
+        cmax[q] = cmax[q + 1] = hi;
+        const int2 r = make_int2((int)(lo / 128), (int)(hi / 128));
+        ranges.push_back(r);
+        L.tile0 = std::min<int64_t>(L.tile0, r.x);
+        L.tile1 = std::max<int64_t>(L.tile1, r.y);
+        L.work_tiles += r.y - r.x + 1;
+      }
+      sc.max_count = std::max(sc.max_count, L.count);
+      sc.launches.push_back(L);
+    }
+  }
+  sc.groups = (int64_t)gjk.size();
+  const size_t bytes = sizeof(int2) * (size_t)std::max<int64_t>(sc.groups, 1);
+  if (cudaMalloc(&sc.d_gjk, bytes) != cudaSuccess || cudaMalloc(&sc.d_ranges, bytes) != cudaSuccess) {
+    bb_schedule_free(&sc);
+    (void)cudaGetLastError();
+    return EVD_ERR_OOM;
+  }
+  if (sc.groups > 0 &&
+      (cudaMemcpy(sc.d_gjk, gjk.data(), sizeof(int2) * gjk.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(sc.d_ranges, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+    bb_schedule_free(&sc);
+    return EVD_ERR_CUDA;
+  }
+  *out = std::move(sc);
+  return EVD_OK;
+}
+
+void bb_schedule_free(BbSchedule* s) {
+  if (!s) return;
+  if (s->d_gjk) cudaFree(s->d_gjk);
+  if (s->d_ranges) cudaFree(s->d_ranges);
+  s->d_gjk = s->d_ranges = nullptr;
+  s->launches.clear();
+}
+
+namespace {
+
+// The fused waves in chunks: the group factors of as many consecutive launches as
+// the scratch holds are prepared in one go, then those launches run.
+evd_status_t fused_waves(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
+                         bool identity) {
+  const BbSchedule& sc = *pc.bb;
+  int64_t cmax = std::min<int64_t>(sc.groups, 65535);
+  while (cmax > sc.max_count && bcback_prep_bytes((int)cmax, pc.ref_slices) > w.gemm_ws_bytes) cmax /= 2;
+  cmax = std::max<int64_t>(cmax, sc.max_count);
+  if (bcback_prep_bytes((int)cmax, pc.ref_slices) > w.gemm_ws_bytes)
+    return ws_fail("bc_back fused prep", w.gemm_ws_bytes, bcback_prep_bytes((int)cmax, pc.ref_slices));
+  size_t i = 0;
+  while (i < sc.launches.size()) {
+    const size_t first = i;
+    int64_t cnt = 0;
+    while (i < sc.launches.size() && cnt + sc.launches[i].count <= cmax) cnt += sc.launches[i++].count;
+    const int64_t g_begin = sc.launches[first].g0;
+    evd_status_t st = bcback_prep_chunk(pc, bw, sc.d_gjk + g_begin, (int)cnt, w.gemm_ws);
+    if (st != EVD_OK) return st;
+    for (size_t l = first; l < i; ++l) {
+      const BbLaunch& L = sc.launches[l];
+      WaveTiles wt;
+      if (identity) {
+        wt.ranges = sc.d_ranges + L.g0;
+        wt.tile0 = L.tile0;
+        wt.tile1 = L.tile1;
+        wt.work_tiles = L.work_tiles;
+      }
+      st = bcback_fused_wave(pc, Q, ldq, w.gemm_ws, (int)cnt, (int)(L.g0 - g_begin), L.count, L.R0, L.hh0, wt);
+      if (st != EVD_OK) return st;
+    }
+  }
+  return EVD_OK;
+}
+
+}  // namespace
+
 evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
-                         int2* ident_ranges) {
+                         bool identity) {
   const int64_t n = pc.n;
-  if (ident_ranges) {
+  if (identity) {
     // BC-Back of the identity (reordered stages): X = I first
     const evd_status_t st = set_identity(Q, ldq, n, pc.stream);
     if (st != EVD_OK) return st;
@@ -195,7 +312,7 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   const size_t smem = ((size_t)h * g + (size_t)g * g + 2 * g) * sizeof(double);
   // small problems, and band widths whose group factors do not fit in shared
   // memory (b > 64): reflector-by-reflector kernel on FP64 cores
-  if (pc.slices <= 0 || n < 1024 || (!w.Vg && !ident_ranges) || smem > kMaxDynamicSmem) {
+  if (pc.slices <= 0 || n < 1024 || (!w.Vg && !identity) || smem > kMaxDynamicSmem) {
     const unsigned grid = (unsigned)ceil_div(n, BB_NC);
     StatScope sc("bc_back", pc.stream, 4.0 * pc.b * (double)n * (double)bc_num_reflectors(n, pc.b));
     k_bc_back<<<grid, BB_NT, 0, pc.stream>>>(bw.U, bw.Utau, n, pc.b, pc.b, Q, ldq); count_launch();
@@ -210,51 +327,16 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
     if (st != EVD_OK) return st;
   }
   auto kc = [&](int64_t J) { return sweep_steps_b(n, b, J * g); };
-  const bool fused = pc.bcback_fused && bcback_fused_supported(pc, Q, ldq);
-  if (ident_ranges && !fused) return EVD_ERR_INVALID_ARG;  // the identity start needs the fused waves
+  const bool fused = pc.bcback_fused && pc.bb && bcback_fused_supported(pc, Q, ldq);
+  if (identity && !fused) return EVD_ERR_INVALID_ARG;  // the identity start needs the fused waves
   if (fused) {
-    const evd_status_t st = bcback_fixed_point(pc, Q, ldq, true);
+    evd_status_t st = bcback_fixed_point(pc, Q, ldq, true);
     if (st != EVD_OK) return st;
+    st = fused_waves(pc, bw, Q, ldq, w, identity);
+    if (st != EVD_OK) return st;
+    return bcback_fixed_point(pc, Q, ldq, false);
   }
   const int64_t tmax = kc(0) + nJ - 2;
-  // Identity start: the column tiles each group's rows can be nonzero in.  X = I
-  // at first, so row r is nonzero in column r only; a group mixes its rows, so
-  // afterwards all of them are nonzero at most over the union of their column
-  // ranges.  With g = b the group G(J, k) covers rows (J+k) b + 1 .. (J+k+2) b - 1,
-  // inside the b-row blocks q = J + k and q + 1 (block q: rows q b + 1 .. q b + b),
-  // and the groups of one launch cover disjoint blocks, so tracking one column
-  // interval per block, in launch order, gives a superset of every group's support.
-  std::vector<int2> ranges;
-  std::vector<int64_t> launch_off;
-  if (ident_ranges) {
-    const int64_t nblk = n / b + 3;
-    std::vector<int64_t> cmin(nblk), cmax(nblk);
-    for (int64_t q = 0; q < nblk; ++q) {
-      cmin[q] = std::min<int64_t>(q * b + 1, n - 1);
-      cmax[q] = std::min<int64_t>(q * b + b, n - 1);
-    }
-    ranges.reserve((size_t)bc_num_groups(n, b));
-    for (int64_t t = 0; t <= tmax; ++t) {
-      int64_t jp = std::min<int64_t>(t, nJ - 1);
-      while (jp >= 0) {
-        if (t - jp >= kc(nJ - 1 - jp)) { --jp; continue; }
-        const int64_t jhi = jp;
-        while (jp >= 0 && t - jp < kc(nJ - 1 - jp)) --jp;
-        const int64_t jlo = jp + 1;
-        launch_off.push_back((int64_t)ranges.size());
-        for (int64_t jq = jlo; jq <= jhi; ++jq) {
-          const int64_t q = (nJ - 1 - jq) + (t - jq);  // J + k
-          const int64_t lo = std::min(cmin[q], cmin[q + 1]), hi = std::max(cmax[q], cmax[q + 1]);
-          cmin[q] = cmin[q + 1] = lo;
-          cmax[q] = cmax[q + 1] = hi;
-          ranges.push_back(make_int2((int)(lo / 128), (int)(hi / 128)));
-        }
-      }
-    }
-    EVD_CUDA_TRY(cudaMemcpyAsync(ident_ranges, ranges.data(), ranges.size() * sizeof(int2), cudaMemcpyHostToDevice,
-                                 s));
-  }
-  size_t launch_idx = 0;
   for (int64_t t = 0; t <= tmax; ++t) {
     // groups of wave t: J' = nJ - 1 - J in [jlo, jhi] with 0 <= k = t - J' < kc(J)
     int64_t jp = std::min<int64_t>(t, nJ - 1);
@@ -265,28 +347,6 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
       while (jp >= 0 && t - jp < kc(nJ - 1 - jp)) --jp;
       const int64_t jlo = jp + 1;
       const int count = (int)(jhi - jlo + 1);
-      // problem 0 (J' = jlo) is the lowest group of the run and the only one that may reach row n
-      const int64_t J0f = nJ - 1 - jlo, k0f = t - jlo;
-      const int64_t R0f = J0f * g + 1 + k0f * b;
-      if (fused) {
-        WaveTiles wt;
-        if (ident_ranges) {
-          const int64_t off = launch_off[launch_idx++];
-          wt.ranges = ident_ranges + off;
-          wt.tile0 = INT64_MAX;
-          wt.tile1 = -1;
-          for (int p = 0; p < count; ++p) {
-            const int2 r = ranges[(size_t)off + p];
-            wt.tile0 = std::min<int64_t>(wt.tile0, r.x);
-            wt.tile1 = std::max<int64_t>(wt.tile1, r.y);
-            wt.work_tiles += r.y - r.x + 1;
-          }
-        }
-        const evd_status_t st = bcback_fused_wave(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0f,
-                                                  (int)std::min<int64_t>(h, n - R0f), wt);
-        if (st != EVD_OK) return st;
-        continue;
-      }
       if ((size_t)count * h * g > w.vg_capacity || (size_t)count * n * g > w.wt_capacity)
         return ws_fail("bc_back wave buffers", w.wt_capacity, (size_t)count * n * g);
       {
@@ -322,7 +382,6 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
       if (st != EVD_OK) return st;
     }
   }
-  if (fused) return bcback_fixed_point(pc, Q, ldq, false);
   return EVD_OK;
 }
 

@@ -597,7 +597,11 @@ evd_status_t bc_run(const PlanCore& pc, const BcWork& w, double* d, double* e, b
     int per_sm = pc.bc_ctas_per_sm;
     if (per_sm <= 0) per_sm = (variant == 2 && inflight > (int64_t)pc.sms * 5 / 2) ? 2 : 1;
     if (pc.sms > 0 && maxG > pc.sms * per_sm) maxG = pc.sms * per_sm;
-    int64_t G = n - 2;
+    // a CTA takes sweeps j = g, g + G, ...: sweep j + G may start once sweep j is
+    // done, about K steps after its start, while the chain lets it start 2 G steps
+    // after sweep j, so G a little above K / lag keeps every CTA busy; more CTAs
+    // only take SMs that concurrent solves could use
+    int64_t G = std::min<int64_t>(n - 2, inflight + inflight / 4 + 2);
     if (G > maxG) G = maxG;
     void* args[] = {&a};
     // model bytes (each step reads and writes its 2b x b window; U written once)

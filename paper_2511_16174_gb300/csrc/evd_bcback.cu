@@ -70,11 +70,11 @@ __device__ __forceinline__ int frexp_exp(int biased_max) { return (biased_max > 
 //                 of Y (A operand of phase 2: M = r, K = i, scale per r)
 // Problem p of wave t is the group J' = jp0 + p, J = nJ - 1 - J', k = t - J'.
 __global__ void __launch_bounds__(256) k_bb_gather(const double* __restrict__ U, const double* __restrict__ Utau,
-                                                   int64_t n, int b, int64_t nJ, int64_t t, int64_t jp0, double* Vg,
+                                                   int64_t n, int b, const int2* __restrict__ gjk, double* Vg,
                                                    double* taug) {
   constexpr int g = BB_G, H = BB_H;
   const int64_t pidx = blockIdx.x;
-  const int64_t J = nJ - 1 - (jp0 + pidx), k = t - (jp0 + pidx);
+  const int64_t J = gjk[pidx].x, k = gjk[pidx].y;
   double* V = Vg + (size_t)pidx * H * g;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < g; i += 8) {
@@ -645,56 +645,86 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
+// Buffers of the prepared groups of one chunk: the slices and scales the waves read
+// (Vb, Yb, eV, eY, kept until the chunk's waves have run), the FP64 factors and the
+// products' scratch.
+struct PrepBufs {
+  __nv_bfloat16* Vb = nullptr;
+  __nv_bfloat16* Yb = nullptr;
+  int* eV = nullptr;
+  int* eY = nullptr;
+  double* Vg = nullptr;
+  double* Yg = nullptr;
+  double* Gg = nullptr;
+  double* Tg = nullptr;
+  double* taug = nullptr;
+  char* scratch = nullptr;
+  size_t bytes = 0;  // total, the products' scratch included
+};
+
+PrepBufs carve_prep(void* base, int count, int ref_slices) {
+  Carver cv(base);
+  PrepBufs b;
+  b.Vb = cv.take<__nv_bfloat16>((size_t)count * 8 * BB_G * BB_H);  // room for 8 slices
+  b.Yb = cv.take<__nv_bfloat16>((size_t)count * 8 * BB_H * BB_G);
+  b.eV = cv.take<int>((size_t)count * BB_G);
+  b.eY = cv.take<int>((size_t)count * BB_H);
+  b.Vg = cv.take<double>((size_t)count * BB_H * BB_G);
+  b.Yg = cv.take<double>((size_t)count * BB_H * BB_G);
+  b.Gg = cv.take<double>((size_t)count * BB_G * BB_G);
+  b.Tg = cv.take<double>((size_t)count * BB_G * BB_G);
+  b.taug = cv.take<double>((size_t)count * BB_G);
+  b.scratch = cv.take<char>(0);
+  const size_t prod = std::max(ozaki_scratch_bytes_batched(BB_G, BB_G, BB_H, ref_slices, count),
+                               ozaki_scratch_bytes_batched(BB_H, BB_G, BB_G, ref_slices, count));
+  b.bytes = cv.off + prod + 256;
+  return b;
+}
+
+// The compact WY factors of `count` groups ((J, k) in gjk) and their slices, in a
+// handful of batched launches (the prep of a whole chunk of waves at once).
 template <int S>
-evd_status_t launch_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w, int64_t nJ,
-                         int64_t t, int64_t jlo, int count, int64_t R0, int hh0, const WaveTiles& wt, cudaStream_t s) {
+evd_status_t prep_groups(const PlanCore& pc, const BcWork& bw, const int2* gjk, int count, const PrepBufs& pb,
+                         cudaStream_t s) {
   const int64_t n = pc.n;
   const int b = pc.b;
-  // workspace: blobs and scales, the FP64 factors, then the products' scratch
-  Carver cv(w.gemm_ws);
-  __nv_bfloat16* Vb = cv.take<__nv_bfloat16>((size_t)count * S * BB_G * BB_H);
-  __nv_bfloat16* Yb = cv.take<__nv_bfloat16>((size_t)count * S * BB_H * BB_G);
-  int* eV = cv.take<int>((size_t)count * BB_G);
-  int* eY = cv.take<int>((size_t)count * BB_H);
-  double* Vg = cv.take<double>((size_t)count * BB_H * BB_G);
-  double* Yg = cv.take<double>((size_t)count * BB_H * BB_G);
-  double* Gg = cv.take<double>((size_t)count * BB_G * BB_G);
-  double* Tg = cv.take<double>((size_t)count * BB_G * BB_G);
-  double* taug = cv.take<double>((size_t)count * BB_G);
-  char* scratch = cv.take<char>(0);
-  const size_t used = cv.off;
-  const size_t prod = std::max(ozaki_scratch_bytes_batched(BB_G, BB_G, BB_H, pc.ref_slices, count),
-                               ozaki_scratch_bytes_batched(BB_H, BB_G, BB_G, pc.ref_slices, count));
-  if (used + prod > w.gemm_ws_bytes) return ws_fail("bc_back fused wave", w.gemm_ws_bytes, used + prod);
-  {
-    StatScope sc("bc_back_prep", s);
-    k_bb_gather<<<(unsigned)count, 256, 0, s>>>(bw.U, bw.Utau, n, b, nJ, t, jlo, Vg, taug); count_launch();
-    EVD_CUDA_TRY(cudaGetLastError());
-    // G_p = V_p^T V_p
-    Gemm gg;
-    gg.status = pc.status; gg.tag = "bc_back_prep";
-    gg.ta = 'T'; gg.m = BB_G; gg.n = BB_G; gg.k = BB_H; gg.A = Vg; gg.lda = BB_H; gg.B = Vg; gg.ldb = BB_H;
-    gg.C = Gg; gg.ldc = BB_G; gg.alpha = 1.0; gg.beta = 0.0;
-    Batch bt;
-    bt.count = count; bt.sA = (int64_t)BB_H * BB_G; bt.sB = (int64_t)BB_H * BB_G; bt.sC = (int64_t)BB_G * BB_G;
-    evd_status_t st = ozaki_gemm_batched(gg, bt, pc.ref_slices, scratch, w.gemm_ws_bytes - used, s);
-    if (st != EVD_OK) return st;
-    const size_t tsmem = 2 * (size_t)BB_G * BB_G * sizeof(double);
-    st = ensure_dynamic_smem((const void*)k_bb_T, tsmem);
-    if (st != EVD_OK) return st;
-    k_bb_T<<<(unsigned)count, BB_G, tsmem, s>>>(Gg, taug, Tg); count_launch();
-    EVD_CUDA_TRY(cudaGetLastError());
-    // Y_p = V_p T_p
-    Gemm gy;
-    gy.status = pc.status; gy.tag = "bc_back_prep";
-    gy.m = BB_H; gy.n = BB_G; gy.k = BB_G; gy.A = Vg; gy.lda = BB_H; gy.B = Tg; gy.ldb = BB_G;
-    gy.C = Yg; gy.ldc = BB_H; gy.alpha = 1.0; gy.beta = 0.0;
-    bt.sA = (int64_t)BB_H * BB_G; bt.sB = (int64_t)BB_G * BB_G; bt.sC = (int64_t)BB_H * BB_G;
-    st = ozaki_gemm_batched(gy, bt, pc.ref_slices, scratch, w.gemm_ws_bytes - used, s);
-    if (st != EVD_OK) return st;
-    k_bb_split<S><<<(unsigned)count, 256, 0, s>>>(Vg, Yg, Vb, eV, Yb, eY); count_launch();
-    EVD_CUDA_TRY(cudaGetLastError());
-  }
+  StatScope sc("bc_back_prep", s);
+  k_bb_gather<<<(unsigned)count, 256, 0, s>>>(bw.U, bw.Utau, n, b, gjk, pb.Vg, pb.taug); count_launch();
+  EVD_CUDA_TRY(cudaGetLastError());
+  const size_t prod_bytes = pb.bytes - (size_t)(pb.scratch - reinterpret_cast<char*>(pb.Vb));
+  // G_p = V_p^T V_p
+  Gemm gg;
+  gg.status = pc.status; gg.tag = "bc_back_prep";
+  gg.ta = 'T'; gg.m = BB_G; gg.n = BB_G; gg.k = BB_H; gg.A = pb.Vg; gg.lda = BB_H; gg.B = pb.Vg; gg.ldb = BB_H;
+  gg.C = pb.Gg; gg.ldc = BB_G; gg.alpha = 1.0; gg.beta = 0.0;
+  Batch bt;
+  bt.count = count; bt.sA = (int64_t)BB_H * BB_G; bt.sB = (int64_t)BB_H * BB_G; bt.sC = (int64_t)BB_G * BB_G;
+  evd_status_t st = ozaki_gemm_batched(gg, bt, pc.ref_slices, pb.scratch, prod_bytes, s);
+  if (st != EVD_OK) return st;
+  const size_t tsmem = 2 * (size_t)BB_G * BB_G * sizeof(double);
+  st = ensure_dynamic_smem((const void*)k_bb_T, tsmem);
+  if (st != EVD_OK) return st;
+  k_bb_T<<<(unsigned)count, BB_G, tsmem, s>>>(pb.Gg, pb.taug, pb.Tg); count_launch();
+  EVD_CUDA_TRY(cudaGetLastError());
+  // Y_p = V_p T_p
+  Gemm gy;
+  gy.status = pc.status; gy.tag = "bc_back_prep";
+  gy.m = BB_H; gy.n = BB_G; gy.k = BB_G; gy.A = pb.Vg; gy.lda = BB_H; gy.B = pb.Tg; gy.ldb = BB_G;
+  gy.C = pb.Yg; gy.ldc = BB_H; gy.alpha = 1.0; gy.beta = 0.0;
+  bt.sA = (int64_t)BB_H * BB_G; bt.sB = (int64_t)BB_G * BB_G; bt.sC = (int64_t)BB_H * BB_G;
+  st = ozaki_gemm_batched(gy, bt, pc.ref_slices, pb.scratch, prod_bytes, s);
+  if (st != EVD_OK) return st;
+  k_bb_split<S><<<(unsigned)count, 256, 0, s>>>(pb.Vg, pb.Yg, pb.Vb, pb.eV, pb.Yb, pb.eY); count_launch();
+  EVD_CUDA_TRY(cudaGetLastError());
+  return EVD_OK;
+}
+
+// One fused wave over `count` prepared groups starting at group g_off of the chunk.
+template <int S>
+evd_status_t launch_wave(const PlanCore& pc, double* Q, int64_t ldq, const PrepBufs& pb, int g_off, int count,
+                         int64_t R0, int hh0, const WaveTiles& wt, cudaStream_t s) {
+  const int64_t n = pc.n;
+  const int b = pc.b;
   const size_t smem = wave_smem_bytes<S>();
   evd_status_t st = ensure_dynamic_smem((const void*)k_bcback_wave<S>, smem);
   if (st != EVD_OK) return st;
@@ -714,13 +744,16 @@ evd_status_t launch_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   }
   a.X = reinterpret_cast<long long*>(Q); a.ldx = ldq; a.n = n; a.R0 = R0; a.gstride = 2 * b; a.h0 = hh0;
   a.h = 2 * b - 1;
-  a.Vb = Vb; a.eV = eV; a.Yb = Yb; a.eY = eY; a.st = pc.status;
+  a.Vb = pb.Vb + (size_t)g_off * S * BB_G * BB_H;
+  a.eV = pb.eV + (size_t)g_off * BB_G;
+  a.Yb = pb.Yb + (size_t)g_off * S * BB_H * BB_G;
+  a.eY = pb.eY + (size_t)g_off * BB_H;
+  a.st = pc.status;
   a.tile0 = wt.ranges ? wt.tile0 : 0;
   a.ranges = wt.ranges;
   const int64_t ntiles = wt.ranges ? wt.tile1 - wt.tile0 + 1 : ceil_div(n, OZ_BM);
   if (ntiles <= 0) return EVD_OK;
   dim3 grid((unsigned)ntiles, (unsigned)count);
-  // executed bf16 flops of the two products (tensor work of one wave)
   // executed tile work (the tiles of the range table, when there is one)
   const double tiles = wt.ranges ? (double)wt.work_tiles : (double)count * ceil_div(n, OZ_BM);
   const double flops = tiles * OZ_BM * 2.0 * (BB_G * BB_H + BB_H * BB_G) * (double)(S * (S + 1) / 2);
@@ -774,29 +807,26 @@ bool bcback_fused_supported(const PlanCore& pc, const double* Q, int64_t ldq) {
          ldq % 2 == 0 && (reinterpret_cast<uintptr_t>(Q) & 15) == 0;
 }
 
-evd_status_t bcback_fused_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
-                               int64_t nJ, int64_t t, int64_t jlo, int count, int64_t R0, int hh0,
-                               const WaveTiles& wt) {
-  if (pc.slices == 8) return launch_wave<8>(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0, hh0, wt, pc.stream);
-  return launch_wave<6>(pc, bw, Q, ldq, w, nJ, t, jlo, count, R0, hh0, wt, pc.stream);
+size_t bcback_prep_bytes(int count, int ref_slices) { return carve_prep(nullptr, count, ref_slices).bytes; }
+
+evd_status_t bcback_prep_chunk(const PlanCore& pc, const BcWork& bw, const int2* gjk, int count, void* buf) {
+  const PrepBufs pb = carve_prep(buf, count, pc.ref_slices);
+  if (pc.slices == 8) return prep_groups<8>(pc, bw, gjk, count, pb, pc.stream);
+  return prep_groups<6>(pc, bw, gjk, count, pb, pc.stream);
+}
+
+evd_status_t bcback_fused_wave(const PlanCore& pc, double* Q, int64_t ldq, void* buf, int chunk_count, int g_off,
+                               int count, int64_t R0, int hh0, const WaveTiles& wt) {
+  const PrepBufs pb = carve_prep(buf, chunk_count, pc.ref_slices);
+  if (pc.slices == 8) return launch_wave<8>(pc, Q, ldq, pb, g_off, count, R0, hh0, wt, pc.stream);
+  return launch_wave<6>(pc, Q, ldq, pb, g_off, count, R0, hh0, wt, pc.stream);
 }
 
 size_t bcback_fused_scratch_bytes(int64_t n, int b, int ref_slices) {
-  const int64_t count = bc_wave_max_groups(n, b);
-  Carver cv(nullptr);
-  cv.take<__nv_bfloat16>((size_t)count * 8 * BB_G * BB_H);
-  cv.take<__nv_bfloat16>((size_t)count * 8 * BB_H * BB_G);
-  cv.take<int>((size_t)count * BB_G);
-  cv.take<int>((size_t)count * BB_H);
-  cv.take<double>((size_t)count * BB_H * BB_G);
-  cv.take<double>((size_t)count * BB_H * BB_G);
-  cv.take<double>((size_t)count * BB_G * BB_G);
-  cv.take<double>((size_t)count * BB_G * BB_G);
-  cv.take<double>((size_t)count * BB_G);
-  cv.take<char>(0);
-  const size_t prod = std::max(ozaki_scratch_bytes_batched(BB_G, BB_G, BB_H, ref_slices, (int)count),
-                               ozaki_scratch_bytes_batched(BB_H, BB_G, BB_G, ref_slices, (int)count));
-  return cv.off + prod + 256;
+  // the prep of a chunk of up to 4096 groups (at least the largest wave)
+  const int64_t groups = bc_num_groups(n, b);
+  const int chunk = (int)std::max<int64_t>(std::min<int64_t>(groups, 4096), bc_wave_max_groups(n, b));
+  return bcback_prep_bytes(chunk, ref_slices) + 256;
 }
 
 }  // namespace evd

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "evd.h"
 
 namespace evd {
@@ -103,6 +105,7 @@ struct PlanCore {
   int order = -1;         // back transformation: 0 conventional, 1 reordered (Sec. 3.3), -1 by size
   bool dc_sync_free = false;  // D&C without host reads (capturable in a CUDA graph)
   void* dc_tree = nullptr;    // device copy of the D&C merge tree (plan-owned), or nullptr
+  const struct BbSchedule* bb = nullptr;  // fused BC-Back schedule (plan-owned), or nullptr
   int* status = nullptr;  // device int[kStatusWords]
 };
 
@@ -158,6 +161,29 @@ struct DcWork {
 };
 evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t ldq,
                     const DcWork& w);
+// The fused BC-Back schedule of a plan (b = 64, n >= 1024), built once at plan
+// creation: the wave launches in order, the (J, k) of every group in launch order
+// (device) and, for BC-Back of the identity, every group's column-tile range
+// (device) with each launch's tile window.
+struct BbLaunch {
+  int64_t R0;        // first row of the launch's group 0
+  int hh0;           // rows of group 0
+  int64_t g0;        // index of group 0 in the tables
+  int count;         // groups of the launch
+  int64_t tile0, tile1, work_tiles;  // identity start: tile window and tiles of its ranges
+};
+struct BbSchedule {
+  std::vector<BbLaunch> launches;
+  int64_t groups = 0;
+  int max_count = 0;
+  int2* d_gjk = nullptr;
+  int2* d_ranges = nullptr;
+};
+// Builds the schedule; allocates and fills its two device tables (cudaMalloc,
+// synchronous copies).  bb_schedule_free releases them.
+evd_status_t bb_schedule_build(int64_t n, int b, BbSchedule* out);
+void bb_schedule_free(BbSchedule* s);
+
 // Bytes of the device copy of the D&C merge tree of order n, and its upload
 // (synchronous; done once per plan).
 size_t dc_tree_bytes(int64_t n);
@@ -179,11 +205,11 @@ struct BackWork {
   void* gemm_ws;
   size_t gemm_ws_bytes;
 };
-// BC-Back, X <- Q_b X.  With ident_ranges (device, bc_num_groups() entries) X is set
-// to the identity first and every fused wave skips the column tiles its groups'
-// rows are still zero in (the reordered stages: Q_b I while D&C runs).
+// BC-Back, X <- Q_b X.  With identity, X is set to the identity first and every
+// fused wave skips the column tiles its groups' rows are still zero in (the
+// reordered stages: Q_b I while D&C runs); this needs the plan's fused schedule.
 evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq,
-                         const BackWork& w, int2* ident_ranges = nullptr);
+                         const BackWork& w, bool identity = false);
 int64_t bc_num_groups(int64_t n, int b);
 // Whether a plan's whole-path solve runs the reordered stages (evd_api.cu).
 bool reordered_stages(const PlanCore& c);
@@ -200,10 +226,16 @@ struct WaveTiles {
   int64_t tile0 = 0, tile1 = -1;
   int64_t work_tiles = 0;        // sum over the groups of their range lengths
 };
-evd_status_t bcback_fused_wave(const PlanCore& pc, const BcWork& bw, double* Q, int64_t ldq, const BackWork& w,
-                               int64_t nJ, int64_t t, int64_t jlo, int count, int64_t R0, int hh0,
-                               const WaveTiles& wt);
-// Scratch the fused waves' prep products need (the group factors of one wave).
+// The fused BC-Back waves in chunks: bcback_prep_chunk forms the compact WY factors
+// and slices of `count` groups ((J, k) in the device table gjk) in `buf`
+// (bcback_prep_bytes(count) bytes); bcback_fused_wave then runs one wave over the
+// groups g_off .. g_off + count - 1 of a chunk of chunk_count prepared groups.
+size_t bcback_prep_bytes(int count, int ref_slices);
+evd_status_t bcback_prep_chunk(const PlanCore& pc, const BcWork& bw, const int2* gjk, int count, void* buf);
+evd_status_t bcback_fused_wave(const PlanCore& pc, double* Q, int64_t ldq, void* buf, int chunk_count, int g_off,
+                               int count, int64_t R0, int hh0, const WaveTiles& wt);
+// Scratch of the fused waves with a dedicated region (reordered stages): the group
+// table and the prep of a chunk of groups.
 size_t bcback_fused_scratch_bytes(int64_t n, int b, int ref_slices);
 evd_status_t sbr_back_run(const PlanCore& pc, const double* A, const double* sbr_T,
                           const double* sbr_tau, double* Q, int64_t ldq, const BackWork& w);

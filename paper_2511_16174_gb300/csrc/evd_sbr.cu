@@ -439,7 +439,10 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
         void* args[] = {&pa};
         StatScope sc("sbr_panel_qr", s, 4.0 * (double)m * bw * bw);
         const int64_t max_rows = (200 * 1024 - 8 * ((int64_t)kb * kb + kb)) / (8 * (int64_t)bw) - 1;
-        int Gs = (int)std::max<int64_t>(ceil_div(m, max_rows), std::min<int64_t>(ceil_div(m, 32), pc.sms));
+        // rows per CTA: at least 128 (a column step is a norm and a rank-1 update of
+        // the CTA's rows, far below a grid barrier's cost), so small panels take few
+        // CTAs and leave the rest of the GPU to concurrent solves
+        int Gs = (int)std::max<int64_t>(ceil_div(m, max_rows), std::min<int64_t>(ceil_div(m, 128), pc.sms));
         if (bw <= 64 && Gs <= pc.sms && Gs <= maxG_smem) {
           const int64_t chunk = ceil_div(m, Gs);
           const size_t smem = ((size_t)(chunk | 1) * bw + (size_t)kb * kb + kb) * sizeof(double);

@@ -62,10 +62,20 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def committed_traffic(kernel_cat, n):
+def dgemm_peak():
+    """The FP64 DGEMM rate measured on this GPU (profiles/fp64_dgemm_peak.json), or None."""
+    p = ROOT / "profiles" / "fp64_dgemm_peak.json"
+    try:
+        return float(json.loads(p.read_text())["tflops"])
+    except Exception:
+        return None
+
+
+def committed_traffic(kernel_cat, n, tiles_per_launch=None):
     """DRAM bytes per launch from a committed ncu summary (profiles/traffic.json),
-    if the kernel's sources are unchanged since the capture and the workload
-    matches (else None)."""
+    if the kernel's sources are unchanged since the capture (else None).  An entry
+    holds either bytes per launch for one n, or bytes per tile (a tile's traffic
+    does not depend on n), scaled here by the tiles one launch processes."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
@@ -74,7 +84,9 @@ def committed_traffic(kernel_cat, n):
     except Exception:
         return None
     ent = d.get("kernels", {}).get(kernel_cat)
-    if not ent or ent.get("n") != n:
+    if not ent:
+        return None
+    if "dram_bytes_per_tile" not in ent and ent.get("n") != n:
         return None
     h = hashlib.sha256()
     for f in ent.get("sources", []):
@@ -85,6 +97,8 @@ def committed_traffic(kernel_cat, n):
         h.update(q.read_bytes())
     if h.hexdigest()[:16] != ent.get("src_hash"):
         return None
+    if "dram_bytes_per_tile" in ent:
+        return None if tiles_per_launch is None else ent["dram_bytes_per_tile"] * tiles_per_launch
     return ent.get("dram_bytes_per_launch")
 
 
@@ -321,13 +335,19 @@ def ours(args):
     # and plain stage names for the other kernels.  Bulge chasing carries both its
     # FP64 flop count and the byte model 16 b n^2 (+4 n^2 for U).
     peaks, peak_kind = load_peaks()
-    dom = max(((k, v) for k, v in st.items() if not k.endswith("/tc_split_prep")), key=lambda kv: kv[1][0],
-              default=None) if st else None
+    # the dominant kernel among the stages on the plan's own streams (in the reordered
+    # order D&C runs beside the back transformation on a low-priority stream, and its
+    # event times include the waiting for SMs there)
+    reordered = plan.option("order") == 1
+    main = {k: v for k, v in st.items()
+            if not k.endswith("/tc_split_prep") and not (reordered and k.startswith("dc_"))}
+    dom = max(main.items(), key=lambda kv: kv[1][0], default=None) if main else None
     roof = None
     if dom:
         cat, (dms, dfl, dby, dca) = dom
         per_launch_ms = dms / max(dca, 1)
-        traffic = committed_traffic(cat, n)
+        tiles = dby / (16.0 * 127 * 128) / max(dca, 1) if cat.startswith("bc_back_wave") else None
+        traffic = committed_traffic(cat, n, tiles)
         secs = dms / 1e3
         if cat.endswith("/tc_split"):
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
@@ -335,6 +355,13 @@ def ours(args):
                     "unit": "TFLOP/s", "traffic": traffic,
                     "peak_source": f"{peak_kind} MEASURED_PEAKS.json bf16_tflops_sustained (executed bf16 flops "
                                    f"of the slice-pair products)"}
+            # the same work as FP64 flops (36 slice pairs per FP64 flop at 8 slices)
+            pairs = 36.0 if args.prec == "fp64" else 21.0
+            roof["fp64_equiv_tflops"] = dfl / pairs / secs / 1e12
+            dg = dgemm_peak()
+            if dg:
+                roof["fp64_dgemm_peak_tflops"] = dg
+                roof["frac_of_dgemm_peak"] = roof["fp64_equiv_tflops"] / dg
         else:
             roof = {"kernel": cat, "bound": "alu", "achieved": dfl / secs / 1e12, "peak": FP64_ALU_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "traffic": traffic,

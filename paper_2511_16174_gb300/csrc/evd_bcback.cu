@@ -273,34 +273,71 @@ __device__ __forceinline__ long long scale_round(long long hi, unsigned long lon
 
 // The exact integer value of an FP32 accumulator v with |v| < 2^22: v + 1.5 * 2^23
 // lies in [2^23, 2^24), where the float's ulp is 1, so the integer is its low
-// mantissa bits (one add and one integer subtract instead of a conversion).
-__device__ __forceinline__ int f2i_exact22(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
+// mantissa bits: bits(v + 1.5 * 2^23) - 0x4B400000.
+constexpr uint32_t kMagicBits = 0x4B400000u;
+
+// d = a * b + c with a 32 x 32 -> 64-bit multiply (the FMA pipe's wide multiply-add),
+// modulo 2^64.
+__device__ __forceinline__ unsigned long long mad_wide_u32(uint32_t a, uint32_t b, unsigned long long c) {
+  unsigned long long d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mad_wide_s32(int a, int b, unsigned long long c) {
+  unsigned long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+// Whether the add trick is exact for diagonal k of a product with K-extent KMAX: top
+// digits are at most 128 in magnitude, the others 64, so accumulator k (the pairs
+// t + u = k) is bounded by KMAX 128^2 for k = 0 and by KMAX (2 128 64 + (k - 1) 64^2)
+// for k >= 1.
+template <int KMAX>
+__host__ __device__ constexpr bool small_diag(int k) {
+  return (long long)KMAX * ((k == 0) ? 128 * 128 : 2 * 128 * 64 + (k - 1) * 64 * 64) < (1ll << 22);
+}
+// Weight 2^(7 (H - k)) of diagonal k in Rh (k <= H) or 2^(7 (L - k)) in Rl.
+template <int S>
+__host__ __device__ constexpr uint32_t diag_weight(int k) {
+  return 1u << (k <= ((S - 1 < 3) ? S - 1 : 3) ? 7 * (((S - 1 < 3) ? S - 1 : 3) - k) : 7 * (S - 1 - k));
+}
+// The starting values of Rh and Rl that cancel the magic offset of the diagonals
+// recovered by the add trick: -0x4B400000 times the sum of their weights.
+template <int S, int KMAX>
+__host__ __device__ constexpr long long magic_start(bool high) {
+  long long w = 0;
+  for (int k = 0; k < S; ++k)
+    if (small_diag<KMAX>(k) && ((k <= ((S - 1 < 3) ? S - 1 : 3)) == high)) w += diag_weight<S>(k);
+  return -(long long)kMagicBits * w;
+}
 
 // Drain the S weight accumulators of this thread's 16 columns (TMEM lane quadrant
-// `quad`, columns 16 q4 .. +15 of each weight) into the two exact sums.  KMAX is
-// the product's K.  Top digits are at most 128 in magnitude, the others 64, so
-// accumulator k (the pairs t + u = k) is bounded by KMAX 128^2 for k = 0 and by
-// KMAX (2 128 64 + (k - 1) 64^2) for k >= 1; below 2^22 the add trick converts it.
+// `quad`, columns 16 q4 .. +15 of each weight) into the two exact sums
+//   Rh = sum_{k <= H} acc_k 2^(7 (H - k)),   Rl = sum_{k > H} acc_k 2^(7 (L - k)).
+// Diagonals within the add trick's range contribute their float's bits, weighted by
+// a wide multiply-add, and the starting values cancel the magic offset; the others
+// (phase 1, k >= 5) take the hardware conversion.  No integer shifts or 64-bit adds
+// are issued on the ALU pipe.
 template <int S, int KMAX>
 __device__ __forceinline__ void drain16(uint32_t tmem, int quad, int q4, long long* Rh, long long* Rl) {
   constexpr int L = S - 1, H = (L < 3) ? L : 3;
 #pragma unroll
-  for (int c = 0; c < 16; ++c) { Rh[c] = 0; Rl[c] = 0; }
+  for (int c = 0; c < 16; ++c) {
+    Rh[c] = magic_start<S, KMAX>(true);
+    Rl[c] = magic_start<S, KMAX>(false);
+  }
 #pragma unroll
   for (int k = 0; k <= L; ++k) {
     float v[16];
     tc_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + q4 * 16), v);
-    const long long bound = (long long)KMAX * ((k == 0) ? 128 * 128 : 2 * 128 * 64 + (k - 1) * 64 * 64);
-    const bool small = bound < (1ll << 22);
-    int iv[16];
+    const uint32_t wk = diag_weight<S>(k);
 #pragma unroll
-    for (int c = 0; c < 16; ++c) iv[c] = small ? f2i_exact22(v[c]) : __float2int_rn(v[c]);
-    if (k <= 3) {
-#pragma unroll
-      for (int c = 0; c < 16; ++c) Rh[c] += (long long)iv[c] << (7 * (H - k));
-    } else {
-#pragma unroll
-      for (int c = 0; c < 16; ++c) Rl[c] += (long long)iv[c] << (7 * (L - k));
+    for (int c = 0; c < 16; ++c) {
+      long long& acc = (k <= H) ? Rh[c] : Rl[c];
+      const unsigned long long a = (unsigned long long)acc;
+      acc = (long long)(small_diag<KMAX>(k) ? mad_wide_u32(__float_as_uint(v[c] + 12582912.0f), wk, a)
+                                             : mad_wide_s32(__float2int_rn(v[c]), (int)wk, a));
     }
   }
 }
@@ -346,8 +383,11 @@ __device__ __forceinline__ void put_digits(uint8_t* blob_ks, int m, int kk0, con
   }
 }
 
+// 576 threads x 112 registers fill the SM's register file with one CTA (which its
+// 207 KB of shared memory makes the only one anyway); below 112 the 16 accumulator
+// sums per thread spill.
 template <int S>
-__global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_constant__ WaveArgs a) {
+__global__ void __maxnreg__(112) k_bcback_wave(const __grid_constant__ WaveArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2;   // one K-step of a 128-row operand (all slices)
@@ -527,9 +567,12 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
         tc_fence_before();
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
+          // the exact 128-bit sum, kept in (Rh, Rl) as (hi, lo) for the rescale below
           long long hi;
           unsigned long long lo, uh, ul;
           sum128<S>(Rh[c], Rl[c], hi, lo);
+          Rh[c] = hi;
+          Rl[c] = (long long)lo;
           const int bl = abs128(hi, lo, uh, ul);
           if (bl > 0) bmax = max(bmax, bl + eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1));
         }
@@ -547,12 +590,8 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
     long long T[16];
     if (ok) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        long long hi;
-        unsigned long long lo;
-        sum128<S>(Rh[c], Rl[c], hi, lo);
-        T[c] = scale_round(hi, lo, eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1) + 7 * S - eW);
-      }
+      for (int c = 0; c < 16; ++c)
+        T[c] = scale_round(Rh[c], (unsigned long long)Rl[c], eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1) + 7 * S - eW);
     }
     const bool upper = quad >= 2;  // columns 64 .. 127: written once half 0's products are done
     if (ok && !upper) {

@@ -16,6 +16,10 @@ amounts clamp at 64); it does not call the CUDA path.
   half-unit add and shifts, matches exact rounding.
 * Recombination: R = Rh 2^(7 (L - H)) + Rl rebuilds the exact sum of the diagonal
   sums sum_k acc_k 2^(7 (L - k)).
+* Drain by wide multiply-adds: starting Rh and Rl at -0x4B400000 times the summed
+  weights of the add-trick diagonals, then adding bits(v + 1.5 * 2^23) times the
+  weight (or the converted integer for the other diagonals), modulo 2^64, gives the
+  same Rh and Rl as the direct sums.
 """
 import random
 
@@ -139,3 +143,35 @@ def test_recombination_is_exact():
             Rl = sum(acc[k] << (7 * (L - k)) for k in range(H + 1, S))
             assert (Rh << (7 * (L - H))) + Rl == sum(acc[k] << (7 * (L - k)) for k in range(S))
             assert -(1 << 63) <= Rh < (1 << 63) and -(1 << 63) <= Rl < (1 << 63)
+
+
+def _small(K, k):
+    return diag_bound(K, k) < (1 << 22)
+
+
+def _bits(v):
+    s = f32(f32(v) + f32(12582912.0))
+    return int(np.array([s], dtype=np.float32).view(np.uint32)[0])
+
+
+def test_drain_by_wide_multiply_add_matches_direct_sums():
+    rng = random.Random(4)
+    for S in (6, 8):
+        L, H = S - 1, min(S - 1, 3)
+        w = [1 << (7 * (H - k)) if k <= H else 1 << (7 * (L - k)) for k in range(S)]
+        for K in (128, 64):
+            start_h = -0x4B400000 * sum(w[k] for k in range(S) if _small(K, k) and k <= H)
+            start_l = -0x4B400000 * sum(w[k] for k in range(S) if _small(K, k) and k > H)
+            for _ in range(3000):
+                acc = [rng.randint(-diag_bound(K, k), diag_bound(K, k)) if rng.random() < 0.9 else
+                       (diag_bound(K, k) if rng.random() < 0.5 else -diag_bound(K, k)) for k in range(S)]
+                uh, ul = start_h & M64, start_l & M64
+                for k in range(S):
+                    term = (_bits(acc[k]) if _small(K, k) else acc[k]) * w[k]
+                    if k <= H:
+                        uh = (uh + term) & M64
+                    else:
+                        ul = (ul + term) & M64
+                signed = lambda x: x - (1 << 64) if x >> 63 else x
+                assert signed(uh) == sum(acc[k] * w[k] for k in range(0, H + 1))
+                assert signed(ul) == sum(acc[k] * w[k] for k in range(H + 1, S))

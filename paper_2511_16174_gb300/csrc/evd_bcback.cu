@@ -383,11 +383,10 @@ __device__ __forceinline__ void put_digits(uint8_t* blob_ks, int m, int kk0, con
   }
 }
 
-// 576 threads x 112 registers fill the SM's register file with one CTA (which its
-// 207 KB of shared memory makes the only one anyway); below 112 the 16 accumulator
-// sums per thread spill.
+// 576 threads are 18 warps, so some of the SM's four sub-partitions hold 5 warps and
+// their 16K registers allow at most 96 per thread.
 template <int S>
-__global__ void __maxnreg__(112) k_bcback_wave(const __grid_constant__ WaveArgs a) {
+__global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_constant__ WaveArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2;   // one K-step of a 128-row operand (all slices)

@@ -1,8 +1,9 @@
 """Host logic of bench.py that decides what the JSON line claims (no GPU).
 
 * The roofline's `traffic` comes from profiles/traffic.json only while the sources
-  the capture was taken from are unchanged and the workload matches; any edit of
-  those sources, or another n, gives null.
+  the capture was taken from are unchanged and the workload matches (bytes per launch
+  for one n, or bytes per tile scaled by the tiles of a launch); any edit of those
+  sources, or another n for a per-launch entry, gives null.
 * The nominal flop count is the stated convention (4n^3/3 + 2n^3).
 """
 import hashlib
@@ -24,9 +25,15 @@ def test_committed_traffic_follows_the_sources_hash():
     ent = json.loads((bench.ROOT / "profiles" / "traffic.json").read_text())["kernels"]
     for cat, e in ent.items():
         unchanged = _sources_hash(bench.ROOT, e["sources"]) == e["src_hash"]
-        got = bench.committed_traffic(cat, e["n"])
-        assert got == (e["dram_bytes_per_launch"] if unchanged else None)
-        assert bench.committed_traffic(cat, e["n"] + 1) is None
+        if "dram_bytes_per_tile" in e:
+            # per-tile entries hold at any n, scaled by the tiles of one launch
+            got = bench.committed_traffic(cat, 49152, tiles_per_launch=1000.0)
+            assert got == (e["dram_bytes_per_tile"] * 1000.0 if unchanged else None)
+            assert bench.committed_traffic(cat, 49152) is None  # no tile count, no figure
+        else:
+            got = bench.committed_traffic(cat, e["n"])
+            assert got == (e["dram_bytes_per_launch"] if unchanged else None)
+            assert bench.committed_traffic(cat, e["n"] + 1) is None
     assert bench.committed_traffic("no such kernel", 49152) is None
 
 

@@ -37,6 +37,23 @@ DEFAULT_N = 49152
 FP64_ALU_PEAK_TFLOPS = 1.26  # FP64 CUDA-core rate of GB300: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz
 
 
+AUTOTUNE_FILE = ROOT / "paper_2511_16174_gb300" / "autotune_gb300.json"
+
+
+def tuned_entry(n, job=1, prec=0):
+    """The autotuner's cached (b, nb) for n's power-of-two bucket in the committed
+    cache (measured on GB300), or None."""
+    try:
+        entries = json.loads(AUTOTUNE_FILE.read_text())
+    except Exception:
+        return None
+    bucket = 1 << int(round(np.log2(max(n, 1))))
+    for e in entries:
+        if e["n_bucket"] == bucket and e["job"] == job and e["prec"] == prec:
+            return e
+    return None
+
+
 def nominal_flops(n):
     return 4.0 * n ** 3 / 3.0 + 2.0 * n ** 3
 
@@ -213,6 +230,8 @@ def ours(args):
     if ws_ > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
+    # plans created with b = nb = 0 take the autotuner's entry for their size
+    os.environ.setdefault("EVD_AUTOTUNE_CACHE", str(AUTOTUNE_FILE))
     from paper_2511_16174_gb300 import evd, inputs
 
     n = args.n
@@ -386,7 +405,13 @@ def ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(n, args.prec), "n": n, "job": "V", "prec": args.prec,
-                       "b": plan.b, "nb": plan.nb, "seconds_per_solve": ms / 1e3,
+                       "b": plan.b, "nb": plan.nb,
+                       "blocking": ("autotuner cache " + os.path.basename(os.environ["EVD_AUTOTUNE_CACHE"])
+                                    if args.b == 0 and args.nb == 0
+                                    and tuned_entry(n, 1, 0 if args.prec == "fp64" else 2) is not None
+                                    and os.path.abspath(os.environ["EVD_AUTOTUNE_CACHE"]) == str(AUTOTUNE_FILE)
+                                    else "library default rule" if args.b == 0 and args.nb == 0 else "given"),
+                       "seconds_per_solve": ms / 1e3,
                        "paper_tflops_4n3": 4.0 * n ** 3 / (ms / 1e3) / 1e12,
                        "refine_iters": plan.option("refine_iters") if args.prec != "fp64" else 0,
                        "order": "reordered (Sec. 3.3)" if plan.option("order") == 1 else "conventional",

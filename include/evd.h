@@ -53,8 +53,9 @@ typedef enum { EVD_VALUES = 0, EVD_VECTORS = 1 } evd_job_t;
  *   EVD_FP64        FP64-accurate products: FP64 operands split into 8 bfloat16
  *                   slices of 7 bits, slice pairs multiplied on tensor cores with
  *                   exact FP32 partial sums, recombined in 64-bit integers.
- *   EVD_SPLIT_BF16  Split precision: 6 slices for those products, then
- *                   Ogita-Aishima refinement with FP64-accurate residual products.
+ *   EVD_SPLIT_BF16  Split precision: 7 slices for SBR's products, 6 for the back
+ *                   transformation's, then Ogita-Aishima refinement with
+ *                   FP64-accurate residual products (D&C merges stay FP64-accurate).
  *   EVD_SPLIT_INT8  Accepted for interface completeness; GB300's INT8 tensor rate
  *                   is far below its BF16 rate, so this returns EVD_ERR_NOT_SUPPORTED.
  * Householder vectors and tau (panel QR, BC), the secular equation and the
@@ -83,9 +84,11 @@ evd_status_t evd_plan_workspace_size(evd_plan_t plan, size_t* bytes);
  * evd_plan_workspace_size and the first stage call (EVD_OPT_SLICES changes the
  * workspace size).  Every option has the default stated here; a value out of its
  * range returns EVD_ERR_INVALID_ARG and leaves the plan unchanged.
- *   EVD_OPT_SLICES        1..8  bfloat16 slices of the dense products of SBR, the
- *                               back transformation and the D&C merges (default 8
- *                               for EVD_FP64, 6 for EVD_SPLIT_BF16).
+ *   EVD_OPT_SLICES        1..8  bfloat16 slices of the back transformation's products
+ *                               (default 8 for EVD_FP64, 6 for EVD_SPLIT_BF16).
+ *   EVD_OPT_SBR_SLICES    1..8  slices of SBR's products, Z formation and trailing
+ *                               update (default 8, 7 for EVD_SPLIT_BF16).  The D&C
+ *                               merges and the refinement residuals always take 8.
  *   EVD_OPT_REFINE_ITERS  0..8  Ogita-Aishima steps after an EVD_SPLIT_BF16 solve
  *                               (default 2; ignored for EVD_FP64).
  *   EVD_OPT_XE_SLICES     1..8  slices of the refinement's X E product; E holds
@@ -114,7 +117,8 @@ typedef enum {
   EVD_OPT_PANEL_CTAS = 4,
   EVD_OPT_XE_SLICES = 5,
   EVD_OPT_BC_CTAS_PER_SM = 6,
-  EVD_OPT_ORDER = 7
+  EVD_OPT_ORDER = 7,
+  EVD_OPT_SBR_SLICES = 8
 } evd_option_t;
 evd_status_t evd_plan_set_option(evd_plan_t plan, evd_option_t option, int value);
 evd_status_t evd_plan_get_option(evd_plan_t plan, evd_option_t option, int* value);
@@ -225,6 +229,14 @@ evd_status_t evd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k
                        double* C, int64_t ldc, int slices, void* ws, size_t ws_bytes,
                        void* stream);
 
+/* Device status of the stand-alone products (evd_dgemm, evd_dgemm_static): a bounded
+ * wait inside the tensor-core product that gave up latches EVD_ERR_TIMEOUT in a status
+ * word after the call has returned EVD_OK.  This call synchronizes `stream`, returns the
+ * first latched error of evd_dgemm's calls since the last query or, if none, that of
+ * the last evd_dgemm_static call on the current device, and clears both words (*info:
+ * the location code, may be NULL). */
+evd_status_t evd_dgemm_status(void* stream, int* info);
+
 /* ---------------------------------------------------------------------------
  * evd_dgemm without a workspace: the same product as evd_dgemm, with the same
  * arguments minus ws/ws_bytes.  The paper has no counterpart.  It serves callers
@@ -234,14 +246,18 @@ evd_status_t evd_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k
  *
  * The scratch is one fixed array in device global memory, EVD_STATIC_SCRATCH_BYTES
  * per device, owned by the library.  The call allocates nothing.  Rules:
- * - A product whose evd_gemm_workspace_size() exceeds EVD_STATIC_SCRATCH_BYTES
- *   returns EVD_ERR_WORKSPACE at once, with no device work.
+ * - A product whose least scratch (that of evd_gemm_workspace_size() with no
+ *   split of K; the product lowers its split count to fit) exceeds
+ *   EVD_STATIC_SCRATCH_BYTES returns EVD_ERR_WORKSPACE at once, with no device work.
  * - Calls that overlap in time race on the shared array: calls on different
  *   streams, or from different host threads, must not be in flight together.
  *   Calls queued one after another on the same stream are safe.
  * - The first call on each device looks up the array's device address, which
- *   may load the module.  Make that first call outside any stream capture.
- * Errors: as evd_dgemm; a lookup failure returns EVD_ERR_CUDA. */
+ *   may load the module.  Make that first call outside any stream capture.  The
+ *   address is kept for the process: it assumes the device is not reset.
+ * Errors: as evd_dgemm; a lookup failure returns EVD_ERR_CUDA.  A device-side
+ * timeout is not part of the return value (the call returns before the kernel
+ * runs): evd_dgemm_status() reads it. */
 #define EVD_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 evd_status_t evd_dgemm_static(char transa, char transb, int64_t m, int64_t n, int64_t k,
                               double alpha, const double* A, int64_t lda, const double* B,

@@ -138,7 +138,8 @@ WsLayout make_layout(const PlanCore& pc, void* ws) {
   L.uni = c.take<char>(ub);
   L.uni_bytes = ub;
   // the D&C merges and the refinement residuals run at ref_slices in every mode
-  size_t gb = std::max(gemm_scratch_bytes(n, n, n, pc.slices), gemm_scratch_bytes(n, n, n, pc.ref_slices));
+  size_t gb = std::max({gemm_scratch_bytes(n, n, n, pc.slices), gemm_scratch_bytes(n, n, n, pc.ref_slices),
+                        gemm_scratch_bytes(n, n, n, pc.sbr_slices)});
   L.gemm_ws = c.take<char>(gb);
   L.gemm_bytes = gb;
   L.total = align_up(c.off, 256);
@@ -278,6 +279,11 @@ void fill_core(PlanCore& c, int64_t n, int64_t lda, evd_job_t job, evd_prec_t pr
   // accurate enough (about 1e-11 at n ~ 1e3) for two refinement steps to resolve
   // clusters of gap 1e-6; with 4 slices (about 1e-7) such clusters stay mixed.
   c.slices = (prec == EVD_SPLIT_BF16) ? 6 : 8;
+  // the reduction's product error is a backward error of A: it leaves a coupling
+  // between nearly equal eigenvalues that the refinement keeps (a pair inside its
+  // threshold is not rotated), so SBR keeps 7 slices (2^-48) in split mode; errors of
+  // the back transformation only perturb X and are refined away
+  c.sbr_slices = (prec == EVD_SPLIT_BF16) ? 7 : 8;
   c.ref_slices = 8;
   c.refine_iters = (prec == EVD_SPLIT_BF16) ? 2 : 0;
 }
@@ -371,6 +377,10 @@ evd_status_t evd_plan_set_option(evd_plan_t p, evd_option_t opt, int value) {
       if (value < 1 || value > 8) return EVD_ERR_INVALID_ARG;
       c.slices = value;
       return EVD_OK;
+    case EVD_OPT_SBR_SLICES:
+      if (value < 1 || value > 8) return EVD_ERR_INVALID_ARG;
+      c.sbr_slices = value;
+      return EVD_OK;
     case EVD_OPT_REFINE_ITERS:
       if (value < 0 || value > 8) return EVD_ERR_INVALID_ARG;
       c.refine_iters = value;
@@ -408,6 +418,7 @@ evd_status_t evd_plan_get_option(evd_plan_t p, evd_option_t opt, int* value) {
   const PlanCore& c = p->core;
   switch (opt) {
     case EVD_OPT_SLICES: *value = c.slices; return EVD_OK;
+    case EVD_OPT_SBR_SLICES: *value = c.sbr_slices; return EVD_OK;
     case EVD_OPT_REFINE_ITERS: *value = c.refine_iters; return EVD_OK;
     case EVD_OPT_BCBACK_FUSED: *value = c.bcback_fused; return EVD_OK;
     case EVD_OPT_BC_KERNEL: *value = c.bc_kernel; return EVD_OK;

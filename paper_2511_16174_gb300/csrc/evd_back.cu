@@ -312,7 +312,7 @@ evd_status_t bc_back_run(const PlanCore& pc, const BcWork& bw, double* Q, int64_
   const size_t smem = ((size_t)h * g + (size_t)g * g + 2 * g) * sizeof(double);
   // small problems, and band widths whose group factors do not fit in shared
   // memory (b > 64): reflector-by-reflector kernel on FP64 cores
-  if (pc.slices <= 0 || n < 1024 || (!w.Vg && !identity) || smem > kMaxDynamicSmem) {
+  if (pc.slices <= 0 || n < 256 || (!w.Vg && !identity) || smem > kMaxDynamicSmem) {
     const unsigned grid = (unsigned)ceil_div(n, BB_NC);
     StatScope sc("bc_back", pc.stream, 4.0 * pc.b * (double)n * (double)bc_num_reflectors(n, pc.b));
     k_bc_back<<<grid, BB_NT, 0, pc.stream>>>(bw.U, bw.Utau, n, pc.b, pc.b, Q, ldq); count_launch();

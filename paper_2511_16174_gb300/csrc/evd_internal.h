@@ -91,7 +91,8 @@ struct PlanCore {
   evd_job_t job = EVD_VALUES;
   evd_prec_t prec = EVD_FP64;
   int b = 32, nb = 32;
-  int slices = 8;         // slices for SBR / back transform / merges
+  int slices = 8;         // slices of the back transformation's products
+  int sbr_slices = 8;     // slices of SBR's products (Z formation, trailing update)
   int ref_slices = 8;     // slices for refinement residual products
   int refine_iters = 0;
   cudaStream_t stream = nullptr;

@@ -544,10 +544,30 @@ size_t ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
   return ozaki_scratch_bytes_batched(m, n, k, slices, 1);
 }
 
+size_t ozaki_scratch_bytes_min(int64_t m, int64_t n, int64_t k, int slices) {
+  return scratch_with_splits(m, n, k, slices, 1, 1);
+}
+
+evd_status_t standalone_status_take(int* code, int* info) {
+  *code = 0;
+  *info = 0;
+  int* d = standalone_status();
+  if (!d) return EVD_OK;  // never allocated: no stand-alone product has run
+  int h[kStatusWords] = {0};
+  EVD_CUDA_TRY(cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost));
+  EVD_CUDA_TRY(cudaMemset(d, 0, sizeof(h)));
+  *code = h[0];
+  *info = h[1];
+  return EVD_OK;
+}
+
+// Products from about 2 x 256 x 256 x 128 flops up run on the tensor cores: GB300's
+// FP64 CUDA cores (about 1.1 TFLOP/s for the whole GPU) make even thin products with
+// a long K slower there than the split product's few launches.
 bool ozaki_eligible(const Gemm& g) {
   if (g.k < 32 || g.m < 16 || g.n < 16) return false;
   if (g.m > (int64_t)1 << 30 || g.n > (int64_t)1 << 30 || g.k > ((int64_t)1 << 17)) return false;
-  return 2.0 * (double)g.m * (double)g.n * (double)g.k >= 6.7e7;
+  return 2.0 * (double)g.m * (double)g.n * (double)g.k >= 1.6e7;
 }
 
 evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void* scratch, size_t scratch_bytes,

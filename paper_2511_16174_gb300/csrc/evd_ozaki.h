@@ -24,6 +24,11 @@ struct Batch {
   int64_t first_k = -1, first_m = -1;
 };
 size_t ozaki_scratch_bytes_batched(int64_t m, int64_t n, int64_t k, int slices, int count);
+// The least scratch of one product (no K-split; the product lowers its split count to
+// what the scratch holds).
+size_t ozaki_scratch_bytes_min(int64_t m, int64_t n, int64_t k, int slices);
+// Read and clear the status word of the stand-alone products (evd_dgemm).
+evd_status_t standalone_status_take(int* code, int* info);
 evd_status_t ozaki_gemm_batched(const Gemm& g, const Batch& bt, int slices, void* scratch, size_t scratch_bytes,
                                 cudaStream_t s);
 bool ozaki_eligible(const Gemm& g);

@@ -377,15 +377,15 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
   auto gemm_tag = [&](Gemm g, const char* tag, bool tc) {
     g.status = pc.status;
     g.tag = tag;
-    return gemm(g, tc ? pc.slices : 0, gws, gws_bytes, s);
+    return gemm(g, tc ? pc.sbr_slices : 0, gws, gws_bytes, s);
   };
   // The Z products of one block all read principal submatrices of the block's
   // stale trailing matrix A(r0:, r0:): with more than one panel per block it is
   // split into slices once, at the block's start, when the scratch holds it next to
   // the largest product a panel runs.
   const size_t panel_scratch =
-      std::max({gemm_scratch_bytes(n, b, 2 * (int64_t)pc.nb, pc.slices), gemm_scratch_bytes(2 * (int64_t)pc.nb, b, n, pc.slices),
-                pc.slices > 0 ? ozaki_presplit_gemm_bytes(n, b, pc.slices) : (size_t)0});
+      std::max({gemm_scratch_bytes(n, b, 2 * (int64_t)pc.nb, pc.sbr_slices), gemm_scratch_bytes(2 * (int64_t)pc.nb, b, n, pc.sbr_slices),
+                pc.sbr_slices > 0 ? ozaki_presplit_gemm_bytes(n, b, pc.sbr_slices) : (size_t)0});
   int64_t p = 0;
   bool done = false;
   while (!done) {
@@ -396,12 +396,12 @@ evd_status_t sbr_run(const PlanCore& pc, double* A, const SbrWork& w) {
     gws_bytes = w.gemm_ws_bytes;
     {
       const int64_t r0b = p * b + b, mb = n - r0b;
-      if (nbp > 1 && b % 16 == 0 && pc.slices > 0 && mb >= 2 * b && mb <= ((int64_t)1 << 17)) {
+      if (nbp > 1 && b % 16 == 0 && pc.sbr_slices > 0 && mb >= 2 * b && mb <= ((int64_t)1 << 17)) {
         Gemm probe;
         probe.m = mb; probe.n = b; probe.k = mb;
-        const size_t need = align_up(ozaki_presplit_bytes(mb, pc.slices), 256);
+        const size_t need = align_up(ozaki_presplit_bytes(mb, pc.sbr_slices), 256);
         if (ozaki_eligible(probe) && need + panel_scratch <= w.gemm_ws_bytes) {
-          const evd_status_t st = ozaki_presplit_sym(A + r0b + r0b * lda, lda, mb, pc.slices, w.gemm_ws, need, "sbr_z",
+          const evd_status_t st = ozaki_presplit_sym(A + r0b + r0b * lda, lda, mb, pc.sbr_slices, w.gemm_ws, need, "sbr_z",
                                                      &pre, s);
           if (st != EVD_OK) return st;
           use_pre = true;

@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "evd_internal.h"
+#include "evd_ozaki.h"
 
 namespace evd {
 namespace {
@@ -53,11 +54,46 @@ evd_status_t static_scratch(unsigned char** out) {
 }
 
 }  // namespace
+
+// Read and clear the status word at the array's front (the last static call's).
+evd_status_t static_status_take(int* code, int* info) {
+  *code = 0;
+  *info = 0;
+  int dev = 0;
+  EVD_CUDA_TRY(cudaGetDevice(&dev));
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (dev >= 0 && dev < kMaxDevices) base = g_static_ptr[dev];
+  }
+  if (!base) return EVD_OK;  // no static call on this device yet
+  int h[kStatusWords] = {0};
+  EVD_CUDA_TRY(cudaMemcpy(h, base, sizeof(h), cudaMemcpyDeviceToHost));
+  EVD_CUDA_TRY(cudaMemset(base, 0, sizeof(h)));
+  *code = h[0];
+  *info = h[1];
+  return EVD_OK;
+}
+
 }  // namespace evd
 
 using namespace evd;
 
 extern "C" {
+
+evd_status_t evd_dgemm_status(void* stream, int* info) {
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return EVD_ERR_CUDA;
+  }
+  int c1 = 0, i1 = 0, c2 = 0, i2 = 0;
+  evd_status_t st = standalone_status_take(&c1, &i1);
+  if (st != EVD_OK) return st;
+  st = static_status_take(&c2, &i2);
+  if (st != EVD_OK) return st;
+  if (info) *info = c1 ? i1 : i2;
+  return static_cast<evd_status_t>(c1 ? c1 : c2);
+}
 
 evd_status_t evd_dgemm_static(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
                               const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
@@ -69,8 +105,10 @@ evd_status_t evd_dgemm_static(char transa, char transb, int64_t m, int64_t n, in
   const int64_t ar = (transa == 'N') ? m : k, br = (transb == 'N') ? k : n;
   if (lda < (ar > 1 ? ar : 1) || ldb < (br > 1 ? br : 1) || ldc < (m > 1 ? m : 1)) return EVD_ERR_INVALID_ARG;
   if (m > 0 && n > 0 && (!C || (k > 0 && (!A || !B)))) return EVD_ERR_INVALID_ARG;
-  // oversize: rejected before touching the device
-  if (gemm_scratch_bytes(m, n, k, slices) > (size_t)EVD_STATIC_SCRATCH_BYTES) return EVD_ERR_WORKSPACE;
+  // oversize: rejected before touching the device.  The least scratch counts (no
+  // K-split): the product lowers its split count to what the array holds.
+  if (slices > 0 && ozaki_scratch_bytes_min(m, n, k, slices) > (size_t)EVD_STATIC_SCRATCH_BYTES)
+    return EVD_ERR_WORKSPACE;
   if (m == 0 || n == 0) return EVD_OK;
   unsigned char* base = nullptr;
   const evd_status_t st = static_scratch(&base);

@@ -29,7 +29,7 @@ _sz = ctypes.c_size_t
 EVD_VALUES, EVD_VECTORS = 0, 1
 EVD_FP64, EVD_SPLIT_INT8, EVD_SPLIT_BF16 = 0, 1, 2
 OPTIONS = {"slices": 0, "refine_iters": 1, "bcback_fused": 2, "bc_kernel": 3, "panel_ctas": 4, "xe_slices": 5,
-           "bc_ctas_per_sm": 6, "order": 7}
+           "bc_ctas_per_sm": 6, "order": 7, "sbr_slices": 8}
 STATUS = ["EVD_OK", "EVD_ERR_INVALID_ARG", "EVD_ERR_WORKSPACE", "EVD_ERR_OOM", "EVD_ERR_CUDA",
           "EVD_ERR_NONFINITE", "EVD_ERR_NO_CONVERGENCE", "EVD_ERR_TIMEOUT", "EVD_ERR_NOT_SUPPORTED"]
 
@@ -55,6 +55,7 @@ _SIGS = {
     "evd_gemm_workspace_size": ([_i64, _i64, _i64, _int, ctypes.POINTER(_sz)], _int),
     "evd_dgemm": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64,
                    _int, _vp, _sz, _vp], _int),
+    "evd_dgemm_status": ([_vp, ctypes.POINTER(_int)], _int),
     "evd_dgemm_static": ([ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp,
                           _i64, _int, _vp], _int),
     "evd_batched_last_graph": ([], _int),
@@ -236,6 +237,13 @@ def dgemm_static(transa, transb, alpha, A, B, beta, C, slices=8, stream=None):
                                  _ld(B), float(beta), _ptr(C), _ld(C), int(slices), _stream_ptr(stream)),
            "evd_dgemm_static")
     return C
+
+
+def dgemm_status(stream=None):
+    """(code, info) of the stand-alone products' device status (evd_dgemm_status)."""
+    info = _int()
+    code = _lib.evd_dgemm_status(_stream_ptr(stream), ctypes.byref(info))
+    return code, info.value
 
 
 def syevd_batched(As, job="V", stream=None):

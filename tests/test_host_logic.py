@@ -75,3 +75,16 @@ def test_gemm_workspace_sizes(lib):
     out = ctypes.c_size_t()
     assert lib.evd_gemm_workspace_size(10, 10, 10, 9, ctypes.byref(out)) == 1  # slices > 8
     assert lib.evd_gemm_workspace_size(-1, 10, 10, 8, ctypes.byref(out)) == 1
+
+
+def test_committed_gb300_cache_answers_the_benchmark_sizes(lib):
+    """The cache measured on GB300 (paper_2511_16174_gb300/autotune_gb300.json) is read
+    by the library itself: the n = 49152 solve of the benchmark takes its entry."""
+    path = build.PKG / "autotune_gb300.json"
+    entries = json.loads(path.read_text())
+    for n in (8192, 16384, 49152):
+        st, b, nb = tune(lib, n, 1, 0, path)
+        bucket = 1 << round(__import__("math").log2(n))
+        e = [x for x in entries if x["n_bucket"] == bucket and x["job"] == 1 and x["prec"] == 0][0]
+        assert (st, b, nb) == (0, e["b"], e["nb"])
+        assert nb % b == 0 and nb <= 16 * b

@@ -58,6 +58,7 @@ def test_static_matches_workspace_entry_point_twice(evd, slices, ta, tb, shape):
         got = Cs.cpu().numpy()
         assert np.all(np.abs(got - ref) <= bound)
         assert np.all(np.abs(got - got_ws) <= 2 * bound)
+    assert evd.dgemm_status() == (0, 0)  # no device-side timeout latched
 
 
 @pytest.mark.gpu
@@ -85,7 +86,7 @@ def test_static_rejects_oversize_before_device_work():
     assert lib.evd_gemm_workspace_size(n, n, n, 8, ctypes.byref(size)) == 0
     assert size.value > STATIC_BYTES
     code = lib.evd_dgemm_static(b"N", b"N", n, n, n, 1.0, fake, n, fake, n, 0.0, fake, n, 8, None)
-    assert code == 2  # EVD_ERR_WORKSPACE
+    assert code == 2  # EVD_ERR_WORKSPACE: even its least scratch (no K-split) exceeds the array
     # invalid arguments are rejected before the capacity check
     assert lib.evd_dgemm_static(b"X", b"N", n, n, n, 1.0, fake, n, fake, n, 0.0, fake, n, 8, None) == 1
     assert lib.evd_dgemm_static(b"N", b"N", n, n, n, 1.0, fake, n, fake, n, 0.0, fake, n, 9, None) == 1

@@ -469,9 +469,20 @@ __global__ void __launch_bounds__(4 * BM, (BM <= 32) ? 4 : 2) k_bulge_chase_carr
       }
       __syncthreads();
       const bool next = (k + 1 < K);
+      if (tau != 0.0) {
+        // w <- w - alpha v (alpha = tau w^T v / 2, formed by every warp)
+        double pv = 0.0;
+        for (int t = lane; t < m; t += 32) pv += wv[t] * v[t];
+        pv = warp_sum(pv);
+        const double alpha = 0.5 * tau * pv;
+        __syncthreads();  // (every warp has read wv)
+        if (tid < m) wv[tid] -= alpha * v[tid];
+        __syncthreads();
+      }
       if (warp == 0 && next) {
-        // ---- look-ahead: step k+1's reflector from the final first column of the
-        // block below; publish its beta entry now
+        // ---- look-ahead, while the other warps update the diagonal block: step
+        // k+1's reflector from the final first column of the block below (the
+        // rank-2 update does not touch that block); publish its beta entry now
         const int m1 = mb;
         double ss = 0.0;
         for (int t = 1 + lane; t < m1; t += 32) { const double x = Bs[t]; ss += x * x; }
@@ -496,20 +507,11 @@ __global__ void __launch_bounds__(4 * BM, (BM <= 32) ? 4 : 2) k_bulge_chase_carr
           for (int t = lane; t < b; t += 32) a.U[(uoff + k + 1) * b + t] = vn[t];
           if (lane == 0) a.Utau[uoff + k + 1] = tau1;
         }
-      }
-      if (tau != 0.0) {
-        // w <- w - alpha v (alpha = tau w^T v / 2, formed by every warp), then the
-        // rank-2 update of the lower triangle
-        double pv = 0.0;
-        for (int t = lane; t < m; t += 32) pv += wv[t] * v[t];
-        pv = warp_sum(pv);
-        const double alpha = 0.5 * tau * pv;
-        __syncthreads();  // (every warp has read wv)
-        if (tid < m) wv[tid] -= alpha * v[tid];
-        __syncthreads();
-#pragma unroll
-        for (int it = 0; it < BM * BM / NT; ++it) {
-          const int idx = tid + it * NT;
+      } else if (tau != 0.0) {
+        // the rank-2 update of the lower triangle, by every warp but the one forming
+        // the next reflector
+        const int t0 = next ? tid - 32 : tid, nt = next ? NT - 32 : NT;
+        for (int idx = t0; idx < BM * BM; idx += nt) {
           const int p = idx % BM, q = idx / BM;
           if (p < m && q <= p) Ds[q * LD + p] -= v[p] * wv[q] + wv[p] * v[q];
         }

@@ -245,30 +245,35 @@ __device__ __forceinline__ unsigned long long shr64(unsigned long long x, uint32
   return r;
 }
 
-// Magnitude (uh, ul) of a signed 128-bit value, and its bit length (0 for zero).
-// Branch-free, so that the 16 values of a thread interleave.
-__device__ __forceinline__ int abs128(long long hi, unsigned long long lo, unsigned long long& uh,
-                                      unsigned long long& ul) {
-  const unsigned long long sg = (unsigned long long)(hi >> 63);  // all ones when negative
-  ul = (lo ^ sg) - sg;
-  uh = ((unsigned long long)hi ^ sg) + ((sg != 0ull && ul == 0ull) ? 1ull : 0ull);
-  const int bh = 64 - __clzll((long long)uh), bl = 64 - __clzll((long long)ul);
-  return uh ? 64 + bh : bl;
+// 64-bit arithmetic shift right with PTX semantics: an amount above 64 is clamped to
+// 64, which gives the sign fill.
+__device__ __forceinline__ long long sar64(long long x, uint32_t k) {
+  long long r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(k));
+  return r;
 }
 
-// T = round_half_away(R 2^d) for a signed 128-bit R with |R 2^d| < 2^62.
-// d >= 0: |R| < 2^(62 - d) sits in the low word.  d = -k < 0: add 2^(k-1) to the
-// magnitude and shift it right by k (k >= 128 gives 0).  Branch-free: the shift
-// amounts out of range clamp to a zero contribution.
-__device__ __forceinline__ long long scale_round(long long hi, unsigned long long lo, int d) {
-  unsigned long long uh, ul;
-  abs128(hi, lo, uh, ul);
+// Bit length of the one's complement of a signed 128-bit value R = hi 2^64 + lo: that
+// of |R| for R >= 0 and of |R| - 1 for R < 0 (one less than |R|'s only when |R| is a
+// power of two); 0 for R = 0 and R = -1.
+__device__ __forceinline__ int bitlen128(long long hi, unsigned long long lo) {
+  const unsigned long long sg = (unsigned long long)(hi >> 63);
+  const unsigned long long h = (unsigned long long)hi ^ sg, l = lo ^ sg;
+  return h ? 128 - __clzll((long long)h) : 64 - __clzll((long long)l);
+}
+
+// T = floor(R 2^d + 1/2), R = hi 2^64 + lo signed 128-bit, |R 2^d| < 2^62: round to
+// nearest, ties toward +infinity.  d >= 0: R sits in the low word, shift it left.
+// d = -k < 0: add 2^(k-1) in two's complement and shift right arithmetically by k;
+// k >= 127 gives 0 (|R| < 2^126).  Branch-free: shift amounts out of range clamp.
+__device__ __forceinline__ long long round_shift(long long hi, unsigned long long lo, int d) {
   const uint32_t k = (uint32_t)(-d);
-  const unsigned long long nl = ul + shl64(1ull, k - 1u);
-  const unsigned long long nh = uh + shl64(1ull, k - 65u) + (nl < ul ? 1ull : 0ull);
-  const unsigned long long mr = shr64(nl, k) | shl64(nh, 64u - k) | shr64(nh, k - 64u);
-  const unsigned long long m = (d >= 0) ? shl64(ul, (uint32_t)d) : mr;
-  return (hi < 0) ? -(long long)m : (long long)m;
+  const unsigned long long nl = lo + shl64(1ull, k - 1u);
+  const long long nh = hi + (long long)shl64(1ull, k - 65u) + (nl < lo ? 1ll : 0ll);
+  const long long low = (long long)(shr64(nl, k) | shl64((unsigned long long)nh, 64u - k));
+  const long long high = sar64(nh, k - 64u);
+  const long long r = (k >= 127u) ? 0ll : ((k < 64u) ? low : high);
+  return (d >= 0) ? (long long)shl64(lo, (uint32_t)d) : r;
 }
 
 // The exact integer value of an FP32 accumulator v with |v| < 2^22: v + 1.5 * 2^23
@@ -568,11 +573,13 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
         for (int c = 0; c < 16; ++c) {
           // the exact 128-bit sum, kept in (Rh, Rl) as (hi, lo) for the rescale below
           long long hi;
-          unsigned long long lo, uh, ul;
+          unsigned long long lo;
           sum128<S>(Rh[c], Rl[c], hi, lo);
           Rh[c] = hi;
           Rl[c] = (long long)lo;
-          const int bl = abs128(hi, lo, uh, ul);
+          // one's complement bit length: a negative power of two scales to exactly
+          // -2^(7S), a top digit of -128, which the digits allow
+          const int bl = bitlen128(hi, lo);
           if (bl > 0) bmax = max(bmax, bl + eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1));
         }
       }
@@ -590,7 +597,7 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
     if (ok) {
 #pragma unroll
       for (int c = 0; c < 16; ++c)
-        T[c] = scale_round(Rh[c], (unsigned long long)Rl[c], eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1) + 7 * S - eW);
+        T[c] = round_shift(Rh[c], (unsigned long long)Rl[c], eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1) + 7 * S - eW);
     }
     const bool upper = quad >= 2;  // columns 64 .. 127: written once half 0's products are done
     if (ok && !upper) {
@@ -631,7 +638,7 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
         long long hi;
         unsigned long long lo;
         sum128<S>(Rh[c], Rl[c], hi, lo);
-        Rh[c] = scale_round(hi, lo, eWs[cb + c] + eYr - 14 - 7 * (S - 1) + 7 * S - 1);
+        Rh[c] = round_shift(hi, lo, eWs[cb + c] + eYr - 14 - 7 * (S - 1) + 7 * S - 1);
       }
       long long* xc2 = xr + (c0 + cb) * a.ldx;
       const int64_t left = a.n - (c0 + cb);

@@ -14,7 +14,11 @@ namespace evd {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+// 32 x 64 tiles of 128 threads (4 x 4 per thread): at 58 registers a CTA takes 7.4K
+// registers, so it fits on an SM beside a fused BC-Back wave CTA (which leaves 10K),
+// and the D&C merges that run during the back transformation use the FP64 pipe the
+// waves leave idle instead of waiting for whole SMs.
+constexpr int BM = 32, BN = 64, BK = 16, NT = 128;
 
 __device__ __forceinline__ double load_a(const Gemm& g, int64_t r, int64_t c) {
   // op(A)(r, c), 0 <= r < m, 0 <= c < k
@@ -31,7 +35,7 @@ __global__ void __launch_bounds__(NT) k_dgemm_simt(const Gemm g) {
   if (g.lower && n0 > m0 + BM - 1) return;  // tile strictly above the diagonal
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -58,7 +62,7 @@ __global__ void __launch_bounds__(NT) k_dgemm_simt(const Gemm g) {
     for (int kk = 0; kk < BK; ++kk) {
       double a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 8 * i];
 #pragma unroll
       for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
 #pragma unroll
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(NT) k_dgemm_simt(const Gemm g) {
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int64_t r = m0 + tx + 16 * i, c = n0 + ty + 16 * j;
+      int64_t r = m0 + tx + 8 * i, c = n0 + ty + 16 * j;
       if (r < g.m && c < g.n && (!g.lower || r >= c)) {
         double* p = g.C + r + c * g.ldc;
         double v = g.alpha * acc[i][j];

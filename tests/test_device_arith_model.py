@@ -12,8 +12,11 @@ amounts clamp at 64); it does not call the CUDA path.
   exact.
 * Digit pairs: the bfloat16 with bits 0x4300 | f is 128 + f for f in [0, 127], and
   subtracting 192 gives the digit f - 64 exactly.
-* Rescale: T = round_half_away(R 2^d) from a signed 128-bit R by magnitude, a
-  half-unit add and shifts, matches exact rounding.
+* Rescale: T = floor(R 2^d + 1/2) from a signed 128-bit R by a half-unit add in
+  two's complement and an arithmetic shift, with PTX's clamped shift amounts, matches
+  exact rounding (to nearest, ties toward +infinity).
+* Scale of W from the one's complement bit length: every scaled value stays within
+  [-2^w, 2^w], the top digit within [-128, 128].
 * Recombination: R = Rh 2^(7 (L - H)) + Rl rebuilds the exact sum of the diagonal
   sums sum_k acc_k 2^(7 (L - k)).
 * Drain by wide multiply-adds: starting Rh and Rl at -0x4B400000 times the summed
@@ -92,45 +95,77 @@ def shr64(x, k):
     return 0 if k >= 64 else (x & M64) >> k
 
 
-def scale_round(hi, lo, d):
-    """The magnitude form: |R| as (uh, ul), add half a unit, shift, restore the sign."""
-    sg = M64 if hi < 0 else 0
-    ul = ((lo ^ sg) - sg) & M64
-    uh = (((hi & M64) ^ sg) + (1 if (sg and ul == 0) else 0)) & M64
+def sar64(x, k):
+    """shr.s64: an amount above 64 clamps to 64 (the sign fill)."""
+    k &= 0xFFFFFFFF
+    x = x - (1 << 64) if x >> 63 else x
+    return x >> min(k, 64)
+
+
+def round_shift(hi, lo, d):
+    """The kernel's two's-complement form: add 2^(k-1), shift right arithmetically."""
+    if d >= 0:
+        v = shl64(lo, d)
+        return v - (1 << 64) if v >> 63 else v
     k = (-d) & 0xFFFFFFFF
-    nl = (ul + shl64(1, (k - 1) & 0xFFFFFFFF)) & M64
-    nh = (uh + shl64(1, (k - 65) & 0xFFFFFFFF) + (1 if nl < ul else 0)) & M64
-    mr = shr64(nl, k) | shl64(nh, (64 - k) & 0xFFFFFFFF) | shr64(nh, (k - 64) & 0xFFFFFFFF)
-    m = shl64(ul, d) if d >= 0 else mr
-    return -m if hi < 0 else m
+    nl = (lo + shl64(1, (k - 1) & 0xFFFFFFFF)) & M64
+    nh = (hi + shl64(1, (k - 65) & 0xFFFFFFFF) + (1 if nl < lo else 0)) & M64
+    low = shr64(nl, k) | shl64(nh, (64 - k) & 0xFFFFFFFF)
+    high = sar64(nh, (k - 64) & 0xFFFFFFFF)
+    r = 0 if k >= 127 else (low if k < 64 else high)
+    r &= M64
+    return r - (1 << 64) if r >> 63 else r
 
 
-def test_scale_round_matches_exact_rounding():
+def bitlen128(hi, lo):
+    sg = M64 if hi < 0 else 0
+    h, l = (hi & M64) ^ sg, lo ^ sg
+    return 64 + h.bit_length() if h else l.bit_length()
+
+
+def _split128(R):
+    Ru = R & ((1 << 128) - 1)
+    hi = Ru >> 64
+    return (hi - (1 << 64) if hi >> 63 else hi), Ru & M64
+
+
+def test_round_shift_is_round_to_nearest_ties_up():
     rng = random.Random(2)
     for _ in range(100000):
-        d = rng.randint(-135, 40)
-        lim = min(62 - d, 126)
+        d = rng.randint(-140, 40)
+        lim = min(62 - d, 125)
         if lim <= 0:
             continue
         R = rng.getrandbits(rng.randint(0, lim - 1))
         if d < 0 and -d - 1 < lim - 1 and rng.random() < 0.1:
-            R = ((R >> -d) << -d) + (1 << (-d - 1))  # an exact tie (still below 2^126)
-        if R >= (1 << 126):
-            continue
+            R = ((R >> -d) << -d) + (1 << (-d - 1))  # an exact tie
         if rng.random() < 0.5:
             R = -R
-        Ru = R & ((1 << 128) - 1)
-        hi = Ru >> 64
-        hi = hi - (1 << 64) if hi >> 63 else hi
-        lo = Ru & M64
-        if d >= 0:
-            exact = R << d
-        else:
-            k = -d
-            a = abs(R)
-            q = (a + (1 << (k - 1))) >> k  # half away from zero on the magnitude
-            exact = -q if R < 0 else q
-        assert scale_round(hi, lo, d) == exact, (R, d)
+        hi, lo = _split128(R)
+        exact = R << d if d >= 0 else (R + (1 << (-d - 1))) >> -d  # floor(R 2^d + 1/2)
+        assert round_shift(hi, lo, d) == exact, (R, d)
+
+
+def test_one_complement_bit_length_keeps_the_top_digit_in_range():
+    """With the scale from the one's complement bit length, every scaled value rounds
+    into [-2^w, 2^w] (w = the digits' total width), and only a negative power of two
+    reaches -2^w: a top digit of magnitude at most 128."""
+    rng = random.Random(5)
+    w = 56
+    for _ in range(50000):
+        p = rng.randint(1, 120)
+        R = rng.getrandbits(p) if rng.random() < 0.9 else (1 << (p - 1))
+        if rng.random() < 0.5:
+            R = -R
+        if R == 0:
+            continue
+        hi, lo = _split128(R)
+        bl = bitlen128(hi, lo)
+        assert bl == (abs(R).bit_length() if R > 0 else (abs(R) - 1).bit_length())
+        T = round_shift(hi, lo, w - bl)
+        assert -(1 << w) <= T <= (1 << w)
+        if T == -(1 << w):
+            assert R < 0 and abs(R) & (abs(R) - 1) == 0
 
 
 def test_recombination_is_exact():

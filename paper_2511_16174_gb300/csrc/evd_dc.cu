@@ -623,6 +623,9 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
   int* d_k = reinterpret_cast<int*>(carve(sizeof(int) * (nmerge + 1)));
   int* d_nrot = reinterpret_cast<int*>(carve(sizeof(int) * (nmerge + 1)));
   int* d_grp = reinterpret_cast<int*>(carve(sizeof(int) * 2 * (nmerge + 1)));
+  // descriptors of one level's small merge products (two per merge), launched together
+  Gemm* d_gd = reinterpret_cast<Gemm*>(carve(sizeof(Gemm) * 2 * (nmerge + 1)));
+  std::vector<Gemm> small_gd;
   if (mb > ((size_t)24 * n + 1024) * sizeof(int)) return ws_fail("dc merge descriptors", ((size_t)24 * n + 1024) * sizeof(int), mb);
   if (pc.dc_tree) {
     // the plan's resident copy of the tree (uploaded once, at plan creation)
@@ -711,6 +714,7 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
       // X = Qn U into the first k columns of the block of Q (the block is free now),
       // as X(0:n1, :) = Qn(0:n1, 0:c1+c2) U(0:c1+c2, :) and
       //    X(n1:m, :) = Qn(n1:m, c1:k)     U(c1:k, :)
+      small_gd.clear();
       for (size_t q = 0; q < cnt && !pc.dc_sync_free; ++q) {
         const int k = hk[q];
         if (k == 0) continue;
@@ -728,12 +732,21 @@ evd_status_t dc_run(const PlanCore& pc, double* d, double* e, double* Q, int64_t
           g.B = w.Umat + (off + j0) + off * n; g.ldb = n;
           g.C = Q + (off + r0) + off * ldq; g.ldc = ldq;
           g.alpha = 1.0; g.beta = 0.0;
+          if (g.m <= 0 || g.n <= 0 || g.k <= 0) continue;
+          if (!ozaki_eligible(g)) {
+            small_gd.push_back(g);  // FP64 CUDA cores, with the level's other small products
+            continue;
+          }
           // FP64-accurate in every mode: the next merge's z is the last row of Q1 and the
           // first of Q2, and a product error at the slice level would blur the tiny
           // entries that deflate
           evd_status_t st = gemm(g, pc.ref_slices, w.gemm_ws, w.gemm_ws_bytes, s);
           if (st != EVD_OK) return st;
         }
+      }
+      {
+        const evd_status_t st = gemm_simt_batched(small_gd.data(), (int)small_gd.size(), d_gd, "dc_merge_gemm", s);
+        if (st != EVD_OK) return st;
       }
     }
     StatScope sc2("dc_merge", s);

@@ -4,6 +4,7 @@
 //  * a plain FP64 CUDA-core kernel (slices == 0), used for small or thin shapes;
 //  * the tensor-core split product (slices 1..8, evd_ozaki.cu), used for the large
 //    contractions of SBR (Eq. 1), the back transformation and the D&C merges.
+#include <algorithm>
 #include <cstdio>
 
 #include "device_util.cuh"
@@ -30,8 +31,22 @@ __device__ __forceinline__ double load_b(const Gemm& g, int64_t r, int64_t c) {
   return (g.tb == 'N') ? g.B[r + c * g.ldb] : g.B[c + r * g.ldb];
 }
 
+__device__ __forceinline__ void dgemm_tile(const Gemm& g, int64_t m0, int64_t n0);
+
 __global__ void __launch_bounds__(NT) k_dgemm_simt(const Gemm g) {
+  dgemm_tile(g, (int64_t)blockIdx.x * BM, (int64_t)blockIdx.y * BN);
+}
+
+// Many independent products in one launch: problem blockIdx.z, its tiles inside the
+// grid of the largest one (the other CTAs leave at once).
+__global__ void __launch_bounds__(NT) k_dgemm_simt_batched(const Gemm* __restrict__ gs) {
+  const Gemm& g = gs[blockIdx.z];
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  if (m0 >= g.m || n0 >= g.n) return;
+  dgemm_tile(g, m0, n0);
+}
+
+__device__ __forceinline__ void dgemm_tile(const Gemm& g, int64_t m0, int64_t n0) {
   if (g.lower && n0 > m0 + BM - 1) return;  // tile strictly above the diagonal
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
@@ -147,6 +162,24 @@ __global__ void k_atb_sum(const double* part, int nchunks, int64_t m, int64_t n,
 }
 
 }  // namespace
+
+evd_status_t gemm_simt_batched(const Gemm* host, int count, Gemm* dev, const char* tag, cudaStream_t s) {
+  if (count <= 0) return EVD_OK;
+  int64_t mt = 0, nt = 0;
+  double flops = 0.0;
+  for (int i = 0; i < count; ++i) {
+    if (host[i].k <= 0 || host[i].lower || host[i].a_sym_lower) return EVD_ERR_INVALID_ARG;
+    mt = std::max<int64_t>(mt, ceil_div(host[i].m, BM));
+    nt = std::max<int64_t>(nt, ceil_div(host[i].n, BN));
+    flops += 2.0 * (double)host[i].m * (double)host[i].n * (double)host[i].k;
+  }
+  if (nt > 65535 || count > 65535) return EVD_ERR_INVALID_ARG;
+  EVD_CUDA_TRY(cudaMemcpyAsync(dev, host, sizeof(Gemm) * count, cudaMemcpyHostToDevice, s));
+  StatScope sc(tag, s, flops, 0.0, "fp64_simt");
+  k_dgemm_simt_batched<<<dim3((unsigned)mt, (unsigned)nt, (unsigned)count), NT, 0, s>>>(dev); count_launch();
+  EVD_CUDA_TRY(cudaGetLastError());
+  return EVD_OK;
+}
 
 size_t gemm_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices) {
   if (slices <= 0) return 0;

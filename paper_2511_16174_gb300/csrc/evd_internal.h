@@ -82,6 +82,11 @@ struct Gemm {
 // Scratch a product needs (bytes) and the call itself.
 size_t gemm_scratch_bytes(int64_t m, int64_t n, int64_t k, int slices);
 evd_status_t gemm(const Gemm& g, int slices, void* scratch, size_t scratch_bytes, cudaStream_t s);
+// `count` small products (no lower / symmetric forms, beta applied) on the FP64 CUDA
+// cores in one launch; the descriptors are copied to `dev` (count Gemm) first, from
+// host memory the call may reuse once it returns.
+evd_status_t gemm_simt_batched(const Gemm* host, int count, Gemm* dev, const char* tag, cudaStream_t s);
+bool ozaki_eligible(const Gemm& g);
 
 // ---------------------------------------------------------------- the plan
 

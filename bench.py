@@ -372,10 +372,15 @@ def ours(args):
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             roof = {"kernel": cat, "bound": "tensor", "achieved": dfl / secs / 1e12, "peak": peak,
                     "unit": "TFLOP/s", "traffic": traffic,
-                    "peak_source": f"{peak_kind} MEASURED_PEAKS.json bf16_tflops_sustained (executed bf16 flops "
-                                   f"of the slice-pair products)"}
-            # the same work as FP64 flops (36 slice pairs per FP64 flop at 8 slices)
-            pairs = 36.0 if args.prec == "fp64" else 21.0
+                    "peak_source": f"{peak_kind} MEASURED_PEAKS.json bf16_tflops_sustained (executed 16-bit "
+                                   f"tensor flops of the slice-pair products: bfloat16 slices in the general "
+                                   f"product, float16 digits in the fused BC-Back waves, both at the bf16 rate)"}
+            # the same work as FP64 flops: slice pairs per FP64 flop (general product: 8
+            # slices, 36 pairs; fused waves: 7 digits, 28 pairs; split precision: 21)
+            if args.prec != "fp64":
+                pairs = 21.0
+            else:
+                pairs = 28.0 if cat.startswith("bc_back_wave") else 36.0
             roof["fp64_equiv_tflops"] = dfl / pairs / secs / 1e12
             dg = dgemm_peak()
             if dg:

@@ -5,7 +5,7 @@
 //     X_p  -= Y_p W_p            (Y_p = V_p T_p)
 // with X_p = X(R0_p : R0_p + h, :), R0_p = R0_0 - p (g + b).  One CTA owns group p
 // and 128 columns c0 .. c0+127 of X and does both products on the tensor cores
-// with the split of the FP64-accurate product (evd_ozaki.cu):
+// as split products with exact integer accumulation:
 //   phase 1  D1[m][i] = sum_r X(R0+r, c0+m) V(r, i)          M = 128, N = g = 64, K = 128
 //            The CTA's converter warps read the fixed-point tile of X, write its
 //            digits straight into shared memory; V's slices come pre-split.
@@ -16,20 +16,28 @@
 //            rounding), Y's slices come pre-split; X(R0 + r, c0 + c) -= D2[r][c].
 //            The accumulator's lanes are rows of X, so each warp of the epilogue
 //            reads and writes 32 consecutive elements of one column.
-// X is kept in fixed point during BC-Back: T = round(x 2^(7S - 1)) in int64, in
+// Digits: S balanced base-256 digits per operand held as float16 (exact for
+// integers up to 2048).  Both products have K <= 128, so every FP32 accumulator
+// of the slice pairs t + u = k stays an exact integer below 2^24 (at most
+// (k + 1) 128 128^2 with digits in [-128, 128]).  S = 7 digits carry 55 bits,
+// as the 8 bfloat16 slices of 7 bits of the general product (evd_ozaki.cu) do,
+// with 28 slice-pair products in place of 36; a digit is a byte of the offset
+// integer, taken with one byte permute.
+// X is kept in fixed point during BC-Back: T = round(x 2^(8S - 1)) in int64, in
 // place of the FP64 values (bcback_fixed_point converts on entry and exit).  X is
-// orthogonal (D&C's eigenvectors times orthogonal reflectors), so |x| < 2 and
-// |T| < 2^(7S).  The split of the X operand is then the integer itself and each
-// update is an exact 128-bit rescale and one int64 subtraction; every update rounds
-// once to the grid 2^(1-7S) (at most 2^-56 at S = 8, far below FP64's
-// product error over the 2n/b waves).  Only the int64 tile of X moves through HBM
-// (read twice, written once): no slice or W buffer is materialized in global memory.
+// orthogonal (D&C's eigenvectors times orthogonal reflectors), so |x| <= 1 and
+// |T| <= 2^(8S - 1).  The split of the X operand is then the integer itself and
+// each update is an exact 128-bit rescale and one int64 subtraction; every update
+// rounds once to the grid 2^(1-8S) (2^-55 at S = 7, far below FP64's product
+// error over the 2n/b waves).  Only the int64 tile of X moves through HBM (read
+// twice, written once): no slice or W buffer is materialized in global memory.
 //
-// Roles (576 threads): warp 0 copies the pre-split blobs (bulk copies), warp 1
-// owns the tensor memory (512 columns) and issues the MMAs, warps 2..17 convert X
-// and W into slices and drain the accumulators (16 accumulator columns per
-// thread).  Every wait is bounded.
+// Roles (576 threads): warp 0 copies (tensor copies of X, up to five K-steps
+// ahead, and the pre-split blobs), warp 1 owns the tensor memory (512 columns) and
+// issues the MMAs, warps 2..17 convert X and W into digits and drain the
+// accumulators (16 accumulator columns per thread).  Every wait is bounded.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -58,6 +66,59 @@ __device__ __forceinline__ int biased_exp(double x) {
 }
 __device__ __forceinline__ int frexp_exp(int biased_max) { return (biased_max > 0) ? biased_max - 1022 : -1022; }
 
+// ---------------------------------------------------------------- 8-bit digits
+// An operand x with frexp exponent e (|x| < 2^e) is the integer
+// T = round_half_away(x 2^(8S - 1 - e)), |T| <= 2^(8S - 1).  With the offset
+// O = 128 (1 + 256 + ... + 256^(S-2)), digit j < S - 1 (from the bottom) of T is
+// byte j of T + O minus 128, in [-128, 127]; the top digit is (T + O) >> 8(S - 1),
+// in [-128, 128].  Slice t holds digit S - 1 - t (slice 0 is the top).
+template <int S>
+__host__ __device__ constexpr long long offset8() {
+  long long o = 0;
+  for (int j = 0; j < S - 1; ++j) o = (o << 8) + 128;
+  return o;
+}
+
+// round_half_away(x 2^p) as an integer (|x 2^p| < 2^62): the general product's
+// scaling with no slices, T = x 2^(0 - e) for e = -p.
+__device__ __forceinline__ long long scaled_pow2(double x, int p) { return ozaki_scaled(x, -p, 0); }
+
+__device__ __forceinline__ uint32_t hsub2_bits(uint32_t a, uint32_t b) {
+  const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&a), *reinterpret_cast<const __half2*>(&b));
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Digit j (0..3 within its 32-bit word) of two offset integers as a float16 pair:
+// the byte f placed under the float16 exponent of 1024 (bits 0x6400 | f, the value
+// 1024 + f exactly), minus 1152 gives the digit f - 128 exactly.
+__device__ __forceinline__ uint32_t digit8_pair(uint32_t wa, uint32_t wb, int j) {
+  const uint32_t f = __byte_perm(wa, wb, (uint32_t)j | ((uint32_t)(4 + j) << 8));
+  return hsub2_bits((f & 0x00FF00FFu) | 0x64006400u, 0x64806480u);
+}
+
+// The top digits d in [-128, 128] of two offset integers as a float16 pair: the
+// bits 0x6480 + d are the float16 1152 + d, minus 1152 gives d.
+__device__ __forceinline__ uint32_t top8_pair(long long TOa, long long TOb, int sh) {
+  const uint32_t a = (uint32_t)(0x6480 + (int)(TOa >> sh)), b = (uint32_t)(0x6480 + (int)(TOb >> sh));
+  return hsub2_bits(__byte_perm(a, b, 0x5410), 0x64806480u);
+}
+
+// Slice tt of NV offset integers TO (NV even) as NV / 2 float16 pairs.
+template <int S, int NV>
+__device__ __forceinline__ void slice8(const long long* TO, int tt, uint32_t* w) {
+#pragma unroll
+  for (int q = 0; q < NV / 2; ++q) {
+    if (tt == 0) {
+      w[q] = top8_pair(TO[2 * q], TO[2 * q + 1], 8 * (S - 1));
+    } else {
+      const int j = S - 1 - tt;  // digit position from the bottom
+      const uint32_t wa = (j < 4) ? (uint32_t)TO[2 * q] : (uint32_t)((unsigned long long)TO[2 * q] >> 32);
+      const uint32_t wb = (j < 4) ? (uint32_t)TO[2 * q + 1] : (uint32_t)((unsigned long long)TO[2 * q + 1] >> 32);
+      w[q] = digit8_pair(wa, wb, j & 3);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- prep
 // The compact WY factors of the wave's groups, with the dense products on the
 // tensor cores:
@@ -66,8 +127,9 @@ __device__ __forceinline__ int frexp_exp(int biased_max) { return (biased_max > 
 //   k_bb_T        T_p upper triangular with H_0 ... H_{g-1} = I - V T V^T:
 //                 T(i, i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i)
 //   product       Y_p = V_p T_p                           (batched split product)
-//   k_bb_split    slices of V (B operand of phase 1: N = i, K = r, scale per i) and
-//                 of Y (A operand of phase 2: M = r, K = i, scale per r)
+//   k_bb_split    8-bit float16 slices of V (B operand of phase 1: N = i, K = r,
+//                 scale per i) and of Y (A operand of phase 2: M = r, K = i, scale
+//                 per r)
 // Problem p of wave t is the group J' = jp0 + p, J = nJ - 1 - J', k = t - J'.
 __global__ void __launch_bounds__(256) k_bb_gather(const double* __restrict__ U, const double* __restrict__ Utau,
                                                    int64_t n, int b, const int2* __restrict__ gjk, double* Vg,
@@ -128,14 +190,14 @@ __global__ void __launch_bounds__(64) k_bb_T(const double* __restrict__ Gg, cons
 
 template <int S>
 __global__ void __launch_bounds__(256) k_bb_split(const double* __restrict__ Vg, const double* __restrict__ Yg,
-                                                  __nv_bfloat16* Vb, int* eV, __nv_bfloat16* Yb, int* eY) {
+                                                  __half* Vb, int* eV, __half* Yb, int* eY) {
   constexpr int g = BB_G, H = BB_H;
+  constexpr long long off = offset8<S>();
   __shared__ int ex_s[H];
   const int tid = threadIdx.x;
   const int64_t pidx = blockIdx.x;
   const double* V = Vg + (size_t)pidx * H * g;
   const double* Y = Yg + (size_t)pidx * H * g;
-  const long long off = ozaki_offset(S);
   if (tid < g) {
     int mx = 0;
     for (int r = 0; r < H; ++r) mx = max(mx, biased_exp(V[r + (size_t)tid * H]));
@@ -143,21 +205,16 @@ __global__ void __launch_bounds__(256) k_bb_split(const double* __restrict__ Vg,
     ex_s[tid] = frexp_exp(mx);
   }
   __syncthreads();
-  __nv_bfloat16* Vp = Vb + (size_t)pidx * S * g * H;
+  __half* Vp = Vb + (size_t)pidx * S * g * H;
   for (int u = tid; u < g * H / 8; u += 256) {
     const int i = u / (H / 8), r0 = (u % (H / 8)) * 8;
     long long TO[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) TO[q] = ozaki_scaled(V[(r0 + q) + (size_t)i * H], ex_s[i], S) + off;
+    for (int q = 0; q < 8; ++q) TO[q] = scaled_pow2(V[(r0 + q) + (size_t)i * H], 8 * S - 1 - ex_s[i]) + off;
+#pragma unroll
     for (int tt = 0; tt < S; ++tt) {
       uint32_t w[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        __nv_bfloat162 h2;
-        h2.x = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q], S, tt));
-        h2.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q + 1], S, tt));
-        w[q] = *reinterpret_cast<uint32_t*>(&h2);
-      }
+      slice8<S, 8>(TO, tt, w);
       *reinterpret_cast<uint4*>(Vp + blob_index(i, r0, tt, S, 64, H / 16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
@@ -169,38 +226,36 @@ __global__ void __launch_bounds__(256) k_bb_split(const double* __restrict__ Vg,
     ex_s[tid] = frexp_exp(mx);
   }
   __syncthreads();
-  __nv_bfloat16* Yp = Yb + (size_t)pidx * S * H * g;
+  __half* Yp = Yb + (size_t)pidx * S * H * g;
   for (int u = tid; u < H * g / 8; u += 256) {
     const int r = u / (g / 8), i0 = (u % (g / 8)) * 8;
     long long TO[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) TO[q] = ozaki_scaled(Y[r + (size_t)(i0 + q) * H], ex_s[r], S) + off;
+    for (int q = 0; q < 8; ++q) TO[q] = scaled_pow2(Y[r + (size_t)(i0 + q) * H], 8 * S - 1 - ex_s[r]) + off;
+#pragma unroll
     for (int tt = 0; tt < S; ++tt) {
       uint32_t w[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        __nv_bfloat162 h2;
-        h2.x = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q], S, tt));
-        h2.y = __float2bfloat16_rn((float)ozaki_digit(TO[2 * q + 1], S, tt));
-        w[q] = *reinterpret_cast<uint32_t*>(&h2);
-      }
+      slice8<S, 8>(TO, tt, w);
       *reinterpret_cast<uint4*>(Yp + blob_index(r, i0, tt, S, 128, g / 16)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
 
 // ---------------------------------------------------------------- fused wave
+constexpr int BB_NX = 5;    // X boxes in flight: the tensor copies of X run up to five K-steps ahead
+constexpr int BB_MAXS = 7;  // digits of the FP64-accurate waves (6 in split precision)
+
 struct WaveArgs {
   CUtensorMap xmap;  // X as a 2-D int64 tensor (rows, columns), box BB_XROWS x 128
-  long long* X;     // X in fixed point: x = T 2^(1 - 7S) (see bcback_fixed_point)
+  long long* X;     // X in fixed point: x = T 2^(1 - 8S) (see bcback_fixed_point)
   int64_t ldx, n;
   int64_t R0;       // first row of group 0
   int64_t gstride;  // rows between consecutive groups (g + b)
   int h0;           // rows of group 0 (the others have h)
   int h;            // rows of a group (2b - 1)
-  const __nv_bfloat16* Vb;
+  const __half* Vb;
   const int* eV;
-  const __nv_bfloat16* Yb;
+  const __half* Yb;
   const int* eY;
   int* st;
   int64_t tile0;       // column tile of blockIdx.x = 0 (tiles of 128 columns)
@@ -219,10 +274,10 @@ __device__ __forceinline__ bool bar_and_epi(bool v) {
 }
 
 // The exact signed 128-bit value (hi, lo) of one accumulator pair:
-// R = Rh 2^(7 (L - H)) + Rl.
+// R = Rh 2^(8 (L - H)) + Rl.
 template <int S>
 __device__ __forceinline__ void sum128(long long rh, long long rl, long long& hi, unsigned long long& lo) {
-  constexpr int L = S - 1, H = (L < 3) ? L : 3, shift_hi = 7 * (L - H);
+  constexpr int L = S - 1, H = (L < 3) ? L : 3, shift_hi = 8 * (L - H);
   lo = (shift_hi == 0) ? (unsigned long long)rh : ((unsigned long long)rh << shift_hi);
   hi = (shift_hi == 0) ? (rh >> 63) : (rh >> (64 - shift_hi));
   if (L >= 4) {
@@ -253,15 +308,6 @@ __device__ __forceinline__ long long sar64(long long x, uint32_t k) {
   return r;
 }
 
-// Bit length of the one's complement of a signed 128-bit value R = hi 2^64 + lo: that
-// of |R| for R >= 0 and of |R| - 1 for R < 0 (one less than |R|'s only when |R| is a
-// power of two); 0 for R = 0 and R = -1.
-__device__ __forceinline__ int bitlen128(long long hi, unsigned long long lo) {
-  const unsigned long long sg = (unsigned long long)(hi >> 63);
-  const unsigned long long h = (unsigned long long)hi ^ sg, l = lo ^ sg;
-  return h ? 128 - __clzll((long long)h) : 64 - __clzll((long long)l);
-}
-
 // T = floor(R 2^d + 1/2), R = hi 2^64 + lo signed 128-bit, |R 2^d| < 2^62: round to
 // nearest, ties toward +infinity.  d >= 0: R sits in the low word, shift it left.
 // d = -k < 0: add 2^(k-1) in two's complement and shift right arithmetically by k;
@@ -276,6 +322,25 @@ __device__ __forceinline__ long long round_shift(long long hi, unsigned long lon
   return (d >= 0) ? (long long)shl64(lo, (uint32_t)d) : r;
 }
 
+// R = Rh 2^G + Rl (G = 8 (L - H)) without forming the 128-bit value:
+// floor(R 2^-k + 1/2) for 0 < k < G, where Rh 2^G is a multiple of 2^k and only the
+// low part rounds (|result| < 2^62).
+template <int G>
+__device__ __forceinline__ long long round_split(long long Rh, long long Rl, int k) {
+  return (long long)((unsigned long long)Rh << (G - k)) + ((Rl + (1ll << (k - 1))) >> k);
+}
+// The bit length of the one's complement of R = Rh 2^G + Rl: that of |R| for R >= 0
+// and of |R| - 1 for R < 0 (one less than |R|'s only when |R| is a power of two); 0
+// for R = 0 and R = -1.  With s = floor(R / 2^G) = Rh + (Rl >> G) it is s's plus G
+// unless s is 0 or -1, when R itself fits in G + 1 bits.
+__device__ __forceinline__ int bitlen64(long long x) { return 64 - __clzll(x ^ (x >> 63)); }
+template <int G>
+__device__ __forceinline__ int bitlen_split(long long Rh, long long Rl) {
+  const long long s = Rh + (Rl >> G);
+  const long long r = (long long)((unsigned long long)s << G) + (Rl & ((1ll << G) - 1));
+  return (s != 0 && s != -1) ? bitlen64(s) + G : bitlen64(r);
+}
+
 // The exact integer value of an FP32 accumulator v with |v| < 2^22: v + 1.5 * 2^23
 // lies in [2^23, 2^24), where the float's ulp is 1, so the integer is its low
 // mantissa bits: bits(v + 1.5 * 2^23) - 0x4B400000.
@@ -288,74 +353,64 @@ __device__ __forceinline__ unsigned long long mad_wide_u32(uint32_t a, uint32_t 
   asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
   return d;
 }
-__device__ __forceinline__ unsigned long long mad_wide_s32(int a, int b, unsigned long long c) {
-  unsigned long long d;
-  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-  return d;
-}
 
-// Whether the add trick is exact for diagonal k of a product with K-extent KMAX: top
-// digits are at most 128 in magnitude, the others 64, so accumulator k (the pairs
-// t + u = k) is bounded by KMAX 128^2 for k = 0 and by KMAX (2 128 64 + (k - 1) 64^2)
-// for k >= 1.
-template <int KMAX>
-__host__ __device__ constexpr bool small_diag(int k) {
-  return (long long)KMAX * ((k == 0) ? 128 * 128 : 2 * 128 * 64 + (k - 1) * 64 * 64) < (1ll << 22);
-}
-// Weight 2^(7 (H - k)) of diagonal k in Rh (k <= H) or 2^(7 (L - k)) in Rl.
+// Weight 2^(8 (H - k)) of diagonal k in Rh (k <= H) or 2^(8 (L - k)) in Rl.
 template <int S>
-__host__ __device__ constexpr uint32_t diag_weight(int k) {
-  return 1u << (k <= ((S - 1 < 3) ? S - 1 : 3) ? 7 * (((S - 1 < 3) ? S - 1 : 3) - k) : 7 * (S - 1 - k));
+__host__ __device__ constexpr uint32_t weight8(int k) {
+  return 1u << (k <= ((S - 1 < 3) ? S - 1 : 3) ? 8 * (((S - 1 < 3) ? S - 1 : 3) - k) : 8 * (S - 1 - k));
 }
-// The starting values of Rh and Rl that cancel the magic offset of the diagonals
-// recovered by the add trick: -0x4B400000 times the sum of their weights.
-template <int S, int KMAX>
-__host__ __device__ constexpr long long magic_start(bool high) {
+// The starting value of Rh (high) or Rl that cancels the magic offset of the add
+// trick: -0x4B400000 times the sum of the weights.
+template <int S>
+__host__ __device__ constexpr long long magic_start8(bool high) {
   long long w = 0;
   for (int k = 0; k < S; ++k)
-    if (small_diag<KMAX>(k) && ((k <= ((S - 1 < 3) ? S - 1 : 3)) == high)) w += diag_weight<S>(k);
+    if ((k <= ((S - 1 < 3) ? S - 1 : 3)) == high) w += weight8<S>(k);
   return -(long long)kMagicBits * w;
 }
 
 // Drain the S weight accumulators of this thread's 16 columns (TMEM lane quadrant
 // `quad`, columns 16 q4 .. +15 of each weight) into the two exact sums
-//   Rh = sum_{k <= H} acc_k 2^(7 (H - k)),   Rl = sum_{k > H} acc_k 2^(7 (L - k)).
-// Diagonals within the add trick's range contribute their float's bits, weighted by
-// a wide multiply-add, and the starting values cancel the magic offset; the others
-// (phase 1, k >= 5) take the hardware conversion.  No integer shifts or 64-bit adds
-// are issued on the ALU pipe.
+//   Rh = sum_{k <= H} acc_k 2^(8 (H - k)),   Rl = sum_{k > H} acc_k 2^(8 (L - k)),
+// every value by the add trick: its float's bits weighted by a wide multiply-add,
+// the starting values cancelling the magic offset.  The trick is exact while
+// v + 1.5 * 2^23 stays in [2^23, 2^24) (|v| <= 2^22), but an accumulator may reach
+// (k + 1) K 2^14, up to 2^24 (K <= KMAX): for the diagonals whose bound reaches
+// 2^22, where a sum left that binade (its exponent field changed) for any lane of the
+// warp, the warp reads the 16 values again and replaces the trick's term by the
+// hardware conversion, exact below 2^24.
 template <int S, int KMAX>
 __device__ __forceinline__ void drain16(uint32_t tmem, int quad, int q4, long long* Rh, long long* Rl) {
   constexpr int L = S - 1, H = (L < 3) ? L : 3;
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
-    Rh[c] = magic_start<S, KMAX>(true);
-    Rl[c] = magic_start<S, KMAX>(false);
+    Rh[c] = magic_start8<S>(true);
+    Rl[c] = magic_start8<S>(false);
   }
 #pragma unroll
   for (int k = 0; k <= L; ++k) {
+    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + q4 * 16);
     float v[16];
-    tc_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(k * OZ_BN + q4 * 16), v);
-    const uint32_t wk = diag_weight<S>(k);
+    tc_ld16(taddr, v);
+    const uint32_t wk = weight8<S>(k);
+    uint32_t bad = 0;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
+      const uint32_t bv = __float_as_uint(v[c] + 12582912.0f);
+      if ((long long)(k + 1) * KMAX * 16384 >= (1ll << 22)) bad |= bv ^ 0x4B000000u;  // else below 2^22 by the bound
       long long& acc = (k <= H) ? Rh[c] : Rl[c];
-      const unsigned long long a = (unsigned long long)acc;
-      acc = (long long)(small_diag<KMAX>(k) ? mad_wide_u32(__float_as_uint(v[c] + 12582912.0f), wk, a)
-                                             : mad_wide_s32(__float2int_rn(v[c]), (int)wk, a));
+      acc = (long long)mad_wide_u32(bv, wk, (unsigned long long)acc);
+    }
+    if (__any_sync(0xffffffffu, (bad >> 23) != 0)) {
+      tc_ld16(taddr, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        long long& acc = (k <= H) ? Rh[c] : Rl[c];
+        acc += (long long)wk * ((long long)__float2int_rn(v[c]) -
+                                ((long long)__float_as_uint(v[c] + 12582912.0f) - (long long)kMagicBits));
+      }
     }
   }
-}
-
-// Digit t >= 1 of two offset integers as a bf16 pair: the 7-bit field f in
-// [0, 127] placed under the exponent of 128 (bits 0x4300 | f, the value 128 + f
-// exactly), minus 192 gives the digit f - 64 exactly.
-__device__ __forceinline__ uint32_t digit_pair(long long TOa, long long TOb, int sh) {
-  const uint32_t fa = (uint32_t)(TOa >> sh) & 127u, fb = (uint32_t)(TOb >> sh) & 127u;
-  const uint32_t w = 0x43004300u | fa | (fb << 16), c192 = 0x43404340u;
-  const __nv_bfloat162 v =
-      __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&w), *reinterpret_cast<const __nv_bfloat162*>(&c192));
-  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 // Write the S digit slices of NV consecutive K-values (already scaled integers T,
@@ -363,7 +418,7 @@ __device__ __forceinline__ uint32_t digit_pair(long long TOa, long long TOb, int
 // K-elements kk0 .. kk0+NV-1 of the blob's K-step.
 template <int S, int NV, int TR>
 __device__ __forceinline__ void put_digits(uint8_t* blob_ks, int m, int kk0, const long long* T) {
-  const long long off = ozaki_offset(S);
+  constexpr long long off = offset8<S>();
   const int core = ((m >> 3) * 2 + (kk0 >> 3)) * 64 + (m & 7) * 8 + (kk0 & 7);  // elements
   long long TO[NV];
 #pragma unroll
@@ -371,17 +426,7 @@ __device__ __forceinline__ void put_digits(uint8_t* blob_ks, int m, int kk0, con
 #pragma unroll
   for (int tt = 0; tt < S; ++tt) {
     uint32_t w[NV / 2];
-#pragma unroll
-    for (int q = 0; q < NV / 2; ++q) {
-      if (tt == 0) {  // the signed top digit (|d| <= 128, exact in bf16), made a float by the add trick
-        const float da = __int_as_float(0x4B400000 + (int)(TO[2 * q] >> (7 * (S - 1)))) - 12582912.0f;
-        const float db = __int_as_float(0x4B400000 + (int)(TO[2 * q + 1] >> (7 * (S - 1)))) - 12582912.0f;
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(da, db);
-        w[q] = *reinterpret_cast<const uint32_t*>(&h2);
-      } else {
-        w[q] = digit_pair(TO[2 * q], TO[2 * q + 1], 7 * (S - 1 - tt));
-      }
-    }
+    slice8<S, NV>(TO, tt, w);
     uint8_t* dst = blob_ks + ((size_t)tt * TR * OZ_KS + core) * 2;
     if (NV == 8) *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2 % (NV / 2)], w[3 % (NV / 2)]);
     else *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
@@ -396,14 +441,15 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2;   // one K-step of a 128-row operand (all slices)
   constexpr uint32_t B_KS = S * OZ_BN * OZ_KS * 2;   // one K-step of a 64-row operand
-  // phase 1: A stages [0, 3 A_KS), B stages, then the X boxes; phase 2: Y (all
+  constexpr int NK = BB_H / OZ_KS;                    // K-steps of phase 1
+  constexpr int G = 8 * ((S - 1) - ((S - 1 < 3) ? S - 1 : 3));  // R = Rh 2^G + Rl
+  // phase 1: A stages [0, 3 A_KS), B stages, then the BB_NX X boxes; phase 2: Y (all
   // K-steps) at 0, one half of W (64 columns, all K-steps) after it
   constexpr uint32_t P1_B = BB_P1_STAGES * A_KS;
   constexpr uint32_t P1_X = P1_B + BB_P1_STAGES * B_KS;
   constexpr uint32_t P2_Y = 0;
   constexpr uint32_t P2_W = 4 * A_KS;
-  constexpr uint32_t DATA = (P1_X + BB_P1_STAGES * BB_XS > P2_W + 4 * B_KS) ? P1_X + BB_P1_STAGES * BB_XS
-                                                                             : P2_W + 4 * B_KS;
+  constexpr uint32_t DATA = (P1_X + BB_NX * BB_XS > P2_W + 4 * B_KS) ? P1_X + BB_NX * BB_XS : P2_W + 4 * B_KS;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + DATA);
   uint64_t* fullA = bars;                          // [3], 16 arrivals (converter warps)
   uint64_t* fullB = bars + 3;                      // [3], 1 arrival + bytes
@@ -413,8 +459,9 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
   uint64_t* fullY = bars + 11;                     // Y copied (1 arrival + bytes)
   uint64_t* acc2 = bars + 12;                      // phase 2 half ready (two phases)
   uint64_t* drained = bars + 13;                   // epilogue drained phase 2 half 0 (16 arrivals)
-  uint64_t* fullX = bars + 14;                     // [3], X box landed (1 arrival + bytes)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 17);
+  uint64_t* fullX = bars + 14;                     // [BB_NX], X box landed (1 arrival + bytes)
+  uint64_t* xfree = fullX + BB_NX;                 // [BB_NX], X box read by the converters (16 arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xfree + BB_NX);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* eVs = reinterpret_cast<int*>(tmem_slot + 4);        // 64
   int* eYs = eVs + BB_G;                                     // 128
@@ -432,15 +479,18 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
   const int64_t c0 = tile * OZ_BM;
   const int64_t R0 = a.R0 - p * a.gstride;
   const int hp = (p == 0) ? a.h0 : a.h;
-  const __nv_bfloat16* Vp = a.Vb + (size_t)p * S * BB_G * BB_H;
-  const __nv_bfloat16* Yp = a.Yb + (size_t)p * S * BB_H * BB_G;
+  const __half* Vp = a.Vb + (size_t)p * S * BB_G * BB_H;
+  const __half* Yp = a.Yb + (size_t)p * S * BB_H * BB_G;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 3; ++i) {
       mbar_init(smem_u32(fullA + i), 16);
       mbar_init(smem_u32(fullB + i), 1);
       mbar_init(smem_u32(empty + i), 1);
+    }
+    for (int i = 0; i < BB_NX; ++i) {
       mbar_init(smem_u32(fullX + i), 1);
+      mbar_init(smem_u32(xfree + i), 16);
     }
     mbar_init(smem_u32(acc1), 1);
     mbar_init(smem_u32(fullW), 8);
@@ -463,35 +513,45 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- copies: per K-step of phase 1 the X box (tensor copy: rows
-      // x0 .. x0 + 17 from the even row x0 = R0 + 16 j - (R0 & 1), columns c0 ..
-      // c0 + 127, zero outside X) and V's slices; then Y
+      // ---------------- copies: the X box of K-step jx (tensor copy: rows x0 .. x0 + 17
+      // from the even row x0 = R0 + 16 jx - (R0 & 1), columns c0 .. c0 + 127, zero
+      // outside X) once the converters have read the box BB_NX K-steps back, and V's
+      // slices of K-step jv once the MMAs are done with its stage.  X goes first: its
+      // copies run BB_NX K-steps ahead of the converters, V's three.
       const uint64_t xmap = reinterpret_cast<uint64_t>(&a.xmap);
-      int issued = 0;
-      for (int j = 0; j < BB_H / OZ_KS; ++j) {
-        const int si = j % 3, round = j / 3;
-        // the converters are done with box si once they have filled A stage si
-        if (round > 0 && !mbar_wait(smem_u32(fullA + si), (round - 1) & 1, abort, a.st, 9100)) break;
-        mbar_expect_tx(smem_u32(fullX + si), BB_XS);
-        const int x0 = (int)(R0 + (int64_t)j * OZ_KS - (R0 & 1)), y0 = (int)c0;
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-            ::"r"(smem_u32(smem + P1_X + si * BB_XS)), "l"(xmap), "r"(x0), "r"(y0), "r"(smem_u32(fullX + si))
-            : "memory");
-        if (round > 0 && !mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9101)) {
-          ++issued;
-          break;
+      int jx = 0, jv = 0;
+      long long spins = 0;
+      while ((jx < NK || jv < NK) && !*abort) {
+        if (jx < NK && (jx < BB_NX || mbar_try(smem_u32(xfree + jx % BB_NX), ((jx / BB_NX) - 1) & 1))) {
+          const int xi = jx % BB_NX;
+          mbar_expect_tx(smem_u32(fullX + xi), BB_XS);
+          const int x0 = (int)(R0 + (int64_t)jx * OZ_KS - (R0 & 1)), y0 = (int)c0;
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+              ::"r"(smem_u32(smem + P1_X + xi * BB_XS)), "l"(xmap), "r"(x0), "r"(y0), "r"(smem_u32(fullX + xi))
+              : "memory");
+          ++jx;
+          continue;
         }
-        mbar_expect_tx(smem_u32(fullB + si), B_KS);
-        bulk_load(smem_u32(smem + P1_B + si * B_KS), Vp + (size_t)j * S * OZ_BN * OZ_KS, B_KS, smem_u32(fullB + si));
-        ++issued;
+        if (jv < NK && (jv < 3 || mbar_try(smem_u32(empty + jv % 3), ((jv / 3) - 1) & 1))) {
+          const int si = jv % 3;
+          mbar_expect_tx(smem_u32(fullB + si), B_KS);
+          bulk_load(smem_u32(smem + P1_B + si * B_KS), Vp + (size_t)jv * S * OZ_BN * OZ_KS, B_KS,
+                    smem_u32(fullB + si));
+          ++jv;
+          continue;
+        }
+        if (++spins > OZ_WAIT_LIMIT) {
+          *abort = 1;
+          dev_set_status(a.st, EVD_ERR_TIMEOUT, 9100);
+        }
       }
       if (*abort) {
         // let the copies already in flight land before the CTA exits
-        for (int j = (issued > 3 ? issued - 3 : 0); j < issued; ++j) {
-          for (long long i = 0; i < OZ_WAIT_LIMIT && !mbar_try(smem_u32(fullX + j % 3), (j / 3) & 1); ++i) {}
+        for (int j = (jx > BB_NX ? jx - BB_NX : 0); j < jx; ++j)
+          for (long long i = 0; i < OZ_WAIT_LIMIT && !mbar_try(smem_u32(fullX + j % BB_NX), (j / BB_NX) & 1); ++i) {}
+        for (int j = (jv > 3 ? jv - 3 : 0); j < jv; ++j)
           for (long long i = 0; i < OZ_WAIT_LIMIT && !mbar_try(smem_u32(fullB + j % 3), (j / 3) & 1); ++i) {}
-        }
       }
       // phase 1 finished reading shared memory before the Y copy may overwrite it
       if (!*abort && mbar_wait(smem_u32(acc1), 0, abort, a.st, 9102)) {
@@ -505,14 +565,14 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
       // ---------------- MMA issue
       const uint64_t dbase = desc_kmajor(smem_u32(smem));
       bool ok = true;
-      for (int j = 0; j < BB_H / OZ_KS && ok; ++j) {
+      for (int j = 0; j < NK && ok; ++j) {
         const int si = j % 3, round = j / 3;
         ok = mbar_wait(smem_u32(fullA + si), round & 1, abort, a.st, 9111) &&
              mbar_wait(smem_u32(fullB + si), round & 1, abort, a.st, 9112);
         if (!ok) break;
         tc_fence_after();
-        issue_stage<S>(tmem, dbase + (uint64_t)((si * A_KS) >> 4), dbase + (uint64_t)((P1_B + si * B_KS) >> 4),
-                       j > 0 ? 1u : 0u);
+        issue_stage<S, true>(tmem, dbase + (uint64_t)((si * A_KS) >> 4),
+                             dbase + (uint64_t)((P1_B + si * B_KS) >> 4), j > 0 ? 1u : 0u);
         tc_commit(smem_u32(empty + si));
       }
       if (ok) tc_commit(smem_u32(acc1));
@@ -524,8 +584,8 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
         if (!ok) break;
         tc_fence_after();
         for (int ks = 0; ks < BB_G / OZ_KS; ++ks)
-          issue_stage<S>(tmem, dbase + (uint64_t)((P2_Y + ks * A_KS) >> 4),
-                         dbase + (uint64_t)((P2_W + ks * B_KS) >> 4), ks > 0 ? 1u : 0u);
+          issue_stage<S, true>(tmem, dbase + (uint64_t)((P2_Y + ks * A_KS) >> 4),
+                               dbase + (uint64_t)((P2_W + ks * B_KS) >> 4), ks > 0 ? 1u : 0u);
         tc_commit(smem_u32(acc2));
       }
     }
@@ -537,26 +597,28 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
     const int ct = threadIdx.x - 64;
     // phase 1 producer mapping: column m = ct / 4, rows 4 kq .. 4 kq + 3 of a K-step
     const int m = ct >> 2, kq = ct & 3;
-    // X is held in fixed point on the grid 2^(1 - 7S): the split of the X operand
-    // with the fixed scale 2^1 is then the integer itself (X is orthogonal, so
-    // |x| < 2 and |T| < 2^(7S)).
-    constexpr int eA = 1;
+    // X is held in fixed point on the grid 2^(1 - 8S): the split of the X operand
+    // (frexp exponent 0, |x| <= 1) is then the integer itself.
     const int xoff = (int)(R0 & 1);  // row R0 + 16 j sits at row xoff of its box
     bool ok = true;
-    for (int j = 0; j < BB_H / OZ_KS; ++j) {
-      const int si = j % 3, round = j / 3;
+    for (int j = 0; j < NK; ++j) {
+      const int si = j % 3, round = j / 3, xi = j % BB_NX;
       long long T[4];
-      if (ok) ok = mbar_wait(smem_u32(fullX + si), round & 1, abort, a.st, 9120);
-      const long long* xs = reinterpret_cast<const long long*>(smem + P1_X + si * BB_XS) + m * BB_XROWS + kq * 4 + xoff;
+      if (ok) ok = mbar_wait(smem_u32(fullX + xi), (j / BB_NX) & 1, abort, a.st, 9120);
+      const long long* xs = reinterpret_cast<const long long*>(smem + P1_X + xi * BB_XS) + m * BB_XROWS + kq * 4 + xoff;
 #pragma unroll
       for (int q = 0; q < 4; ++q) T[q] = (ok && j * OZ_KS + kq * 4 + q < hp) ? xs[q] : 0ll;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(xfree + xi));  // the box may be refilled
       if (ok && round > 0) ok = mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9121);
       if (ok) put_digits<S, 4, OZ_BM>(smem + si * A_KS, m, kq * 4, T);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       ok = __all_sync(0xffffffffu, ok);
       if (ok && lane == 0) mbar_arrive(smem_u32(fullA + si));
     }
-    // phase 1 result: W^T(m2, i), i = 16 q4 .. +15, as exact 128-bit integers
+    // phase 1 result: W^T(m2, i), i = 16 q4 .. +15, as exact 128-bit integers R with
+    // W^T = R 2^(eV_i - 8S - 6) (X on the grid 2^(1 - 8S), V_i's digits scaled by
+    // 2^(8S - 1 - eV_i), the diagonal sums weighted from the lowest diagonal up)
     const int quad = warp & 3, q4 = (warp - 2) >> 2;
     const int m2 = quad * 32 + lane;
     if (ok) ok = mbar_wait(smem_u32(acc1), 0, abort, a.st, 9122);
@@ -567,20 +629,14 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
       int bmax = -100000;  // max over this thread's columns of bitlen(R) + scale
       if (ok) {
         tc_fence_after();
-        drain16<S, BB_H>(tmem, quad, q4, Rh, Rl);
+        drain16<S, BB_H - 1>(tmem, quad, q4, Rh, Rl);
         tc_fence_before();
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          // the exact 128-bit sum, kept in (Rh, Rl) as (hi, lo) for the rescale below
-          long long hi;
-          unsigned long long lo;
-          sum128<S>(Rh[c], Rl[c], hi, lo);
-          Rh[c] = hi;
-          Rl[c] = (long long)lo;
           // one's complement bit length: a negative power of two scales to exactly
-          // -2^(7S), a top digit of -128, which the digits allow
-          const int bl = bitlen128(hi, lo);
-          if (bl > 0) bmax = max(bmax, bl + eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1));
+          // -2^(8S - 1), a top digit of -128, which the digits allow
+          const int bl = bitlen_split<G>(Rh[c], Rl[c]);
+          if (bl > 0) bmax = max(bmax, bl + eVs[q4 * 16 + c] - 8 * S - 6);
         }
       }
       // row scale of W^T over its 64 columns (the four quarters meet in shared memory)
@@ -590,14 +646,31 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
       eW = (e4 > -100000) ? e4 : -1022;
     }
     if (q4 == 0) eWs[m2] = eW;
-    // W(i, m2), i = 16 q4 .. +15, scaled to the integer grid of its column
-    // (integer rescaling of the exact sums, no FP64 round trip): K-step q4 of the
-    // B operand of phase 2, half m2 / 64 of the columns
+    // W(i, m2), i = 16 q4 .. +15, as the integers round(W 2^(8S - 1 - eW)) of its
+    // column's scale (integer rescaling of the exact sums, no FP64 round trip):
+    // K-step q4 of the B operand of phase 2, half m2 / 64 of the columns
     long long T[16];
     if (ok) {
+      // T = round(R 2^-k), k = eW + 7 - eV_i: by the split form when every lane's k
+      // lies in (0, G), else through the 128-bit value
+      bool fast = true;
 #pragma unroll
-      for (int c = 0; c < 16; ++c)
-        T[c] = round_shift(Rh[c], (unsigned long long)Rl[c], eA + eVs[q4 * 16 + c] - 14 - 7 * (S - 1) + 7 * S - eW);
+      for (int c = 0; c < 16; ++c) {
+        const int k = eW + 7 - eVs[q4 * 16 + c];
+        fast &= (k > 0) & (k < G);
+      }
+      if (__all_sync(0xffffffffu, fast)) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) T[c] = round_split<G>(Rh[c], Rl[c], eW + 7 - eVs[q4 * 16 + c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          long long hi;
+          unsigned long long lo;
+          sum128<S>(Rh[c], Rl[c], hi, lo);
+          T[c] = round_shift(hi, lo, eVs[q4 * 16 + c] - 7 - eW);
+        }
+      }
     }
     const bool upper = quad >= 2;  // columns 64 .. 127: written once half 0's products are done
     if (ok && !upper) {
@@ -631,14 +704,25 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
       tc_fence_before();
       __syncwarp();
       if (hf == 0 && lane == 0) mbar_arrive(smem_u32(drained));
-      // delta = R 2^(eW_c + eY_r - 14 - 7L) on the grid 2^(1 - 7S), rounded once
+      // D2 = R 2^(eW_c + eY_r - 8S - 6), on the grid 2^(1 - 8S): rounded once
       const int cb = 64 * hf + 16 * q4;
+      bool fast = true;
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        long long hi;
-        unsigned long long lo;
-        sum128<S>(Rh[c], Rl[c], hi, lo);
-        Rh[c] = round_shift(hi, lo, eWs[cb + c] + eYr - 14 - 7 * (S - 1) + 7 * S - 1);
+        const int k = 7 - eWs[cb + c] - eYr;
+        fast &= (k > 0) & (k < G);
+      }
+      if (__all_sync(0xffffffffu, fast)) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) Rh[c] = round_split<G>(Rh[c], Rl[c], 7 - eWs[cb + c] - eYr);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          long long hi;
+          unsigned long long lo;
+          sum128<S>(Rh[c], Rl[c], hi, lo);
+          Rh[c] = round_shift(hi, lo, eWs[cb + c] + eYr - 7);
+        }
       }
       long long* xc2 = xr + (c0 + cb) * a.ldx;
       const int64_t left = a.n - (c0 + cb);
@@ -667,9 +751,8 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
 template <int S>
 size_t wave_smem_bytes() {
   constexpr uint32_t A_KS = S * OZ_BM * OZ_KS * 2, B_KS = S * OZ_BN * OZ_KS * 2;
-  constexpr uint32_t P1 = BB_P1_STAGES * A_KS + BB_P1_STAGES * B_KS, P2 = 4 * A_KS + 4 * B_KS;
-  constexpr uint32_t P1X = P1 + BB_P1_STAGES * BB_XS;
-  return 1024 + (P1X > P2 ? P1X : P2) + 17 * 8 + 16 + (BB_G + BB_H + 5 * BB_H) * 4 + 64;
+  constexpr uint32_t P1X = BB_P1_STAGES * (A_KS + B_KS) + BB_NX * BB_XS, P2 = 4 * A_KS + 4 * B_KS;
+  return 1024 + (P1X > P2 ? P1X : P2) + (14 + 2 * BB_NX) * 8 + 16 + (BB_G + BB_H + 5 * BB_H) * 4 + 64;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the
@@ -694,8 +777,8 @@ EncodeTiledFn encode_tiled() {
 // (Vb, Yb, eV, eY, kept until the chunk's waves have run), the FP64 factors and the
 // products' scratch.
 struct PrepBufs {
-  __nv_bfloat16* Vb = nullptr;
-  __nv_bfloat16* Yb = nullptr;
+  __half* Vb = nullptr;
+  __half* Yb = nullptr;
   int* eV = nullptr;
   int* eY = nullptr;
   double* Vg = nullptr;
@@ -710,8 +793,8 @@ struct PrepBufs {
 PrepBufs carve_prep(void* base, int count, int ref_slices) {
   Carver cv(base);
   PrepBufs b;
-  b.Vb = cv.take<__nv_bfloat16>((size_t)count * 8 * BB_G * BB_H);  // room for 8 slices
-  b.Yb = cv.take<__nv_bfloat16>((size_t)count * 8 * BB_H * BB_G);
+  b.Vb = cv.take<__half>((size_t)count * BB_MAXS * BB_G * BB_H);  // room for the most digits
+  b.Yb = cv.take<__half>((size_t)count * BB_MAXS * BB_H * BB_G);
   b.eV = cv.take<int>((size_t)count * BB_G);
   b.eY = cv.take<int>((size_t)count * BB_H);
   b.Vg = cv.take<double>((size_t)count * BB_H * BB_G);
@@ -809,7 +892,7 @@ evd_status_t launch_wave(const PlanCore& pc, double* Q, int64_t ldq, const PrepB
   return EVD_OK;
 }
 
-// X (FP64, in place) <-> fixed point T = round_half_away(x 2^(7S - 1)) (int64).
+// X (FP64, in place) <-> fixed point T = round_half_away(x 2^(8S - 1)) (int64).
 template <int S>
 __global__ void k_x_fixed(double* Q, int64_t ldq, int64_t n, int to_fixed) {
   const int64_t j = blockIdx.y;
@@ -817,11 +900,11 @@ __global__ void k_x_fixed(double* Q, int64_t ldq, int64_t n, int to_fixed) {
     double* p = Q + i + j * ldq;
     if (to_fixed) {
       const double x = *p;
-      const long long T = ozaki_scaled(x, 1, S);
+      const long long T = scaled_pow2(x, 8 * S - 1);
       *reinterpret_cast<long long*>(p) = T;
     } else {
       const long long T = *reinterpret_cast<const long long*>(p);
-      *p = (double)T * (1.0 / (double)(1ll << (7 * S - 1)));
+      *p = (double)T * (1.0 / (double)(1ll << (8 * S - 1)));
     }
   }
 }
@@ -842,7 +925,7 @@ evd_status_t fixed_point(double* Q, int64_t ldq, int64_t n, bool to_fixed, cudaS
 
 evd_status_t bcback_fixed_point(const PlanCore& pc, double* Q, int64_t ldq, bool to_fixed) {
   StatScope sc("bc_back_prep", pc.stream);
-  return (pc.slices == 8) ? fixed_point<8>(Q, ldq, pc.n, to_fixed, pc.stream)
+  return (pc.slices == 8) ? fixed_point<7>(Q, ldq, pc.n, to_fixed, pc.stream)
                           : fixed_point<6>(Q, ldq, pc.n, to_fixed, pc.stream);
 }
 
@@ -856,14 +939,14 @@ size_t bcback_prep_bytes(int count, int ref_slices) { return carve_prep(nullptr,
 
 evd_status_t bcback_prep_chunk(const PlanCore& pc, const BcWork& bw, const int2* gjk, int count, void* buf) {
   const PrepBufs pb = carve_prep(buf, count, pc.ref_slices);
-  if (pc.slices == 8) return prep_groups<8>(pc, bw, gjk, count, pb, pc.stream);
+  if (pc.slices == 8) return prep_groups<7>(pc, bw, gjk, count, pb, pc.stream);
   return prep_groups<6>(pc, bw, gjk, count, pb, pc.stream);
 }
 
 evd_status_t bcback_fused_wave(const PlanCore& pc, double* Q, int64_t ldq, void* buf, int chunk_count, int g_off,
                                int count, int64_t R0, int hh0, const WaveTiles& wt) {
   const PrepBufs pb = carve_prep(buf, chunk_count, pc.ref_slices);
-  if (pc.slices == 8) return launch_wave<8>(pc, Q, ldq, pb, g_off, count, R0, hh0, wt, pc.stream);
+  if (pc.slices == 8) return launch_wave<7>(pc, Q, ldq, pb, g_off, count, R0, hh0, wt, pc.stream);
   return launch_wave<6>(pc, Q, ldq, pb, g_off, count, R0, hh0, wt, pc.stream);
 }
 

@@ -194,9 +194,12 @@ __device__ __forceinline__ double i128_to_double(long long hi, unsigned long lon
 // descriptor is the stage's base descriptor plus a constant (the 14-bit address
 // field cannot carry: shared-memory addresses stay below 2^18 bytes).  The first
 // products into each weight (t = 0) take acc_t0 (0 at the start of a drain chunk).
-template <int S>
+// F16: both operands float16 (the fused BC-Back waves' 8-bit digits) instead of
+// bfloat16.
+template <int S, bool F16 = false>
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t da0, uint64_t db0, uint32_t acc_t0) {
-  constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
+  constexpr uint32_t kFmt = F16 ? 0u : (1u << 7) | (1u << 10);  // A and B format: 0 float16, 1 bfloat16
+  constexpr uint32_t kIdesc = (1u << 4) | kFmt | ((uint32_t)(OZ_BM >> 4) << 24);
 #pragma unroll
   for (int t = 0; t < S; ++t) {
 #pragma unroll

@@ -195,7 +195,7 @@ void bb_schedule_free(BbSchedule* s);
 size_t dc_tree_bytes(int64_t n);
 evd_status_t dc_tree_upload(int64_t n, void* dst, size_t bytes);
 
-constexpr int kSbrBackPanels = 16;  // SBR panels merged into one compact WY group in SBR-Back
+constexpr int kSbrBackPanels = 32;  // SBR panels merged into one compact WY group in SBR-Back
 struct BackWork {
   double* Tg;      // T factors of the BC reflector groups
   double* Vg;      // V of the BC reflector groups of one wave (count x h x g)

@@ -376,11 +376,12 @@ def ours(args):
                                    f"tensor flops of the slice-pair products: bfloat16 slices in the general "
                                    f"product, float16 digits in the fused BC-Back waves, both at the bf16 rate)"}
             # the same work as FP64 flops: slice pairs per FP64 flop (general product: 8
-            # slices, 36 pairs; fused waves: 7 digits, 28 pairs; split precision: 21)
-            if args.prec != "fp64":
-                pairs = 21.0
+            # slices, 36 pairs, 6 in split precision, 21 pairs; fused waves: 7 digits,
+            # 28 pairs, in both precisions)
+            if cat.startswith("bc_back_wave"):
+                pairs = 28.0
             else:
-                pairs = 28.0 if cat.startswith("bc_back_wave") else 36.0
+                pairs = 36.0 if args.prec == "fp64" else 21.0
             roof["fp64_equiv_tflops"] = dfl / pairs / secs / 1e12
             dg = dgemm_peak()
             if dg:

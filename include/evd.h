@@ -52,10 +52,13 @@ typedef enum { EVD_VALUES = 0, EVD_VECTORS = 1 } evd_job_t;
  * of Eq. 1, the back-transformation GEMMs and the divide-and-conquer merges).
  *   EVD_FP64        FP64-accurate products: FP64 operands split into 8 bfloat16
  *                   slices of 7 bits, slice pairs multiplied on tensor cores with
- *                   exact FP32 partial sums, recombined in 64-bit integers.
- *   EVD_SPLIT_BF16  Split precision: 7 slices for SBR's products, 6 for the back
- *                   transformation's, then Ogita-Aishima refinement with
- *                   FP64-accurate residual products (D&C merges stay FP64-accurate).
+ *                   exact FP32 partial sums, recombined in 64-bit integers.  The
+ *                   fused BC-Back waves (b = 64) use 7 float16 digits of 8 bits
+ *                   (55 bits) with the same exact accumulation.
+ *   EVD_SPLIT_BF16  Split precision: 7 slices for SBR's products, 6 for SBR-Back
+ *                   and the final product (the fused BC-Back waves keep their 7
+ *                   digits), then Ogita-Aishima refinement with FP64-accurate
+ *                   residual products (D&C merges stay FP64-accurate).
  *   EVD_SPLIT_INT8  Accepted for interface completeness; GB300's INT8 tensor rate
  *                   is far below its BF16 rate, so this returns EVD_ERR_NOT_SUPPORTED.
  * Householder vectors and tau (panel QR, BC), the secular equation and the
@@ -85,7 +88,9 @@ evd_status_t evd_plan_workspace_size(evd_plan_t plan, size_t* bytes);
  * workspace size).  Every option has the default stated here; a value out of its
  * range returns EVD_ERR_INVALID_ARG and leaves the plan unchanged.
  *   EVD_OPT_SLICES        1..8  bfloat16 slices of the back transformation's products
- *                               (default 8 for EVD_FP64, 6 for EVD_SPLIT_BF16).
+ *                               (default 8 for EVD_FP64, 6 for EVD_SPLIT_BF16).  At 8
+ *                               or 6 the fused BC-Back waves run with their 7 digits;
+ *                               other values take the batched BC-Back products.
  *   EVD_OPT_SBR_SLICES    1..8  slices of SBR's products, Z formation and trailing
  *                               update (default 8, 7 for EVD_SPLIT_BF16).  The D&C
  *                               merges and the refinement residuals always take 8.

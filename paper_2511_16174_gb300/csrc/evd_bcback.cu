@@ -19,8 +19,8 @@
 // Digits: S balanced base-256 digits per operand held as float16 (exact for
 // integers up to 2048).  Both products have K <= 128, so every FP32 accumulator
 // of the slice pairs t + u = k stays an exact integer below 2^24 (at most
-// (k + 1) 128 128^2 with digits in [-128, 128]).  S = 7 digits carry 55 bits,
-// as the 8 bfloat16 slices of 7 bits of the general product (evd_ozaki.cu) do,
+// (k + 1) 128 128^2 with digits in [-128, 128]).  S = 7 digits carry 55 bits
+// (the 8 bfloat16 slices of 7 bits of the general product, evd_ozaki.cu, carry 56)
 // with 28 slice-pair products in place of 36; a digit is a byte of the offset
 // integer, taken with one byte permute.
 // X is kept in fixed point during BC-Back: T = round(x 2^(8S - 1)) in int64, in

@@ -608,6 +608,9 @@ __global__ void __launch_bounds__(BB_THREADS, 1) k_bcback_wave(const __grid_cons
       const long long* xs = reinterpret_cast<const long long*>(smem + P1_X + xi * BB_XS) + m * BB_XROWS + kq * 4 + xoff;
 #pragma unroll
       for (int q = 0; q < 4; ++q) T[q] = (ok && j * OZ_KS + kq * 4 + q < hp) ? xs[q] : 0ll;
+      // the reads of the box (generic proxy) are ordered before the tensor copy that
+      // refills it (async proxy) by a proxy fence in every reading thread
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(xfree + xi));  // the box may be refilled
       if (ok && round > 0) ok = mbar_wait(smem_u32(empty + si), (round - 1) & 1, abort, a.st, 9121);
@@ -936,9 +939,10 @@ evd_status_t fixed_point(double* Q, int64_t ldq, int64_t n, bool to_fixed, cudaS
 
 }  // namespace
 
-// The fused waves run with 7 digits (55 bits) in both precisions: a 6-digit build of
-// the wave kernel gave run-to-run differences in split precision at n = 16384 whose
-// cause was not found, so it is not instantiated.
+// The fused waves run with 7 digits (55 bits) in both precisions.  A 6-digit build
+// gave run-to-run differences in split precision at n = 16384 until the proxy fence
+// before an X box is released; with it, repeated solves agree bit for bit, but the
+// 6-digit build is not validated at full size and is not instantiated.
 constexpr int kWaveDigits = 7;
 
 evd_status_t bcback_fixed_point(const PlanCore& pc, double* Q, int64_t ldq, bool to_fixed) {
